@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the plain single-text multi-pattern search.
+
+Workload: 1 GiB text of English-like Zipf letters with spaces, 100 patterns of
+lengths 4..32 from the same process, each planted at density 1e-6 per byte
+(seeded, synthetic; the paper's DNA files are not available).  One step is one
+pass of the whole hot path over the resident text: the scan (staging, hashing,
+probing, verification, emission) and the sort into (pattern id, offset) order.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is text GB/s (1e9 bytes/s) with the
+text resident in HBM; `e2e` repeats the measurement through the host-buffer
+call (host->device copy of the text and device->host copy of the sorted list
+inside the timed region).  Under torchrun each rank searches its own copy of
+the workload (independent problems, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "text GB/s scanned (plain single-text multi-pattern search, sorted match list)"
+UNIT = "GB/s"
+WORKLOAD = "zipf_text_1GiB_100_patterns_len4-32_density1e-6"
+SCAN_SRC = os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", "rk_scan.cu")
+PROFILE = os.path.join(ROOT, "profiles", "rk_scan_zipf_1GiB.md")
+CPU_SAMPLE_PER_CORE = 8 << 20   # bytes per core for the oracle baseline
+SLICE_HALO_NOTE = "each slice carries (longest pattern - 1) extra bytes"
+
+
+# ---------------------------------------------------------------- helpers
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def config_dict(n, k):
+    return {"workload": WORKLOAD, "text_bytes": n, "patterns": k, "pattern_len": "4..32",
+            "alphabet": "a-z Zipf(s=1) + space p=1/6", "plant_density": 1e-6,
+            "l2": "text (1 GiB) larger than the 129 MB L2; no flush needed"}
+
+
+def _oracle_slice(args):
+    text_bytes, patterns = args
+    import oracle  # noqa: WPS433  (worker process)
+    t0 = time.perf_counter()
+    ids, _ = oracle.rabin_karp(np.frombuffer(text_bytes, dtype=np.uint8), patterns)
+    return time.perf_counter() - t0, int(ids.size)
+
+
+def cpu_slices(text, lmax, per_core, cores, seed=11):
+    rng = np.random.default_rng(seed)
+    n = text.size
+    starts = rng.integers(0, n - per_core - lmax, cores)
+    return [text[s:s + per_core + lmax - 1].tobytes() for s in starts]
+
+
+def time_oracle(pool, slices, patterns):
+    t0 = time.perf_counter()
+    pool.map(_oracle_slice, [(s, patterns) for s in slices])
+    return time.perf_counter() - t0
+
+
+def read_profile_traffic():
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current scan kernel source (else None)."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m_src = re.search(r"scan_source_sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_src and m_tr):
+        return None
+    cur = hashlib.sha256(open(SCAN_SRC, "rb").read()).hexdigest()
+    return float(m_tr.group(1)) if m_src.group(1) == cur else None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sms.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import build as oracle_build
+    from workloads import make_config
+    oracle_build.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        w = make_config(1)
+        lmax = max(len(p) for p in w.patterns)
+        # calibrate one core, then size each step to keep the run within minutes
+        cal = cpu_slices(w.text, lmax, 256 << 10, 1, seed=3)
+        t_cal = time_oracle(pool, cal, w.patterns)
+        rate = (256 << 10) / max(t_cal, 1e-6)
+        budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))
+        per_core = int(min(16 << 20, max(64 << 10, rate * budget)))
+        for i in range(args.warmup):
+            time_oracle(pool, cpu_slices(w.text, lmax, per_core, cores, seed=100 + i), w.patterns)
+        times = []
+        for i in range(args.steps):
+            times.append(time_oracle(pool, cpu_slices(w.text, lmax, per_core, cores, seed=200 + i),
+                                     w.patterns))
+    total = sum(times)
+    value = cores * per_core * args.steps / total / 1e9
+    sample = (f"{cores} slices of {per_core} bytes per step (one per core) at random offsets of "
+              f"the 1 GiB text; {SLICE_HALO_NOTE}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": config_dict(w.n, len(w.patterns)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def sort_launches(n, k):
+    def bits(v):
+        return int(v).bit_length()
+    passes = (bits(n - 1) + 7) // 8 + (bits(k - 1) + 7) // 8
+    return 3 * passes + (passes % 2)
+
+
+def run_ours(args, rank, world, local_rank):
+    from oracle import build as oracle_build
+    from workloads import make_config
+
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    pool = None
+    cores = os.cpu_count() or 1
+    if want_cpu:
+        oracle_build.build()
+        pool = mp.get_context("spawn").Pool(cores)  # before the first GPU call
+
+    import torch
+    import torch.distributed as dist
+    from paper_1810_01051_gb300 import build_lib, rk
+
+    build_lib.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = make_config(1)
+    n, k = w.n, len(w.patterns)
+    t0 = time.perf_counter()
+    table = rk.rk_build(w.patterns)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    info_t = rk.rk_table_info(table)
+
+    d_text = torch.from_numpy(w.text).to(dev)
+    st = torch.cuda.Stream(dev)
+    d_info = torch.zeros(2, dtype=torch.int64, device=dev)
+
+    # size the output from one probe run
+    cap = 1 << 22
+    while True:
+        keys = torch.empty(cap, dtype=torch.int64, device=dev)
+        wsb = rk.rk_workspace_bytes(table, cap)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        rk.rk_search_device(table, d_text, n, keys, cap, d_info, ws, wsb, st)
+        st.synchronize()
+        m, status = (int(v) for v in d_info.cpu().tolist())
+        assert status == rk.RK_OK, rk.strerror(status)
+        if m <= cap:
+            break
+        cap = m + 1024
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(st)
+        rk.rk_scan_device(table, d_text, n, keys, cap, d_info, st)
+        if evs:
+            evs[1].record(st)
+        rk.rk_sort_device(table, n, keys, cap, d_info, ws, wsb, st)
+        if evs:
+            evs[2].record(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev_start = torch.cuda.Event(enable_timing=True)
+    ev_end = torch.cuda.Event(enable_timing=True)
+    ev_start.record(st)
+    for i in range(args.steps):
+        step(evs[i])
+    ev_end.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = ev_start.elapsed_time(ev_end)
+    scan_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sort_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    m = int(d_info[0].item())
+
+    # end to end through the host-buffer call: pinned text in, sorted list out
+    h_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_text.numpy()[:] = w.text
+    h_keys = torch.empty(cap, dtype=torch.int64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    rk.rk_search(table, h_text, n, h_keys, cap)  # warm the cached device buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc, cnt = rk.rk_search(table, h_text, n, h_keys, cap)
+        assert rc == rk.RK_OK and cnt == m
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    clocks = sampler.stop()
+
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+
+    rk.rk_destroy(table)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    step_ms = total_ms / args.steps
+    value = world * n * args.steps / (total_ms / 1e3) / 1e9
+    scan_mean_s = statistics.mean(scan_ms) / 1e3
+    alg_bytes = n + 8 * m
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    achieved = alg_bytes / scan_mean_s / 1e9
+    traffic = read_profile_traffic()
+
+    cpu = None
+    if pool is not None:
+        lmax = max(len(p) for p in w.patterns)
+        slices = cpu_slices(w.text, lmax, CPU_SAMPLE_PER_CORE, cores)
+        wall = time_oracle(pool, slices, w.patterns)
+        pool.close()
+        cpu = {"value": cores * CPU_SAMPLE_PER_CORE / wall / 1e9, "unit": UNIT, "cores": cores,
+               "kind": "oracle",
+               "sample": f"{cores} slices of {CPU_SAMPLE_PER_CORE} bytes (one per core) at random "
+                         f"offsets of the 1 GiB text, all 100 patterns; {SLICE_HALO_NOTE}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": dict(config_dict(n, k), parallelism=f"replicas{world}"),
+        "matches": m,
+        "scan_ms": statistics.mean(scan_ms), "sort_ms": statistics.mean(sort_ms),
+        "scan_ms_p10_p90": [float(np.percentile(scan_ms, 10)), float(np.percentile(scan_ms, 90))],
+        "hbm_frac_whole_step": (n + 8 * m) / (step_ms / 1e3) / 1e9 / peak,
+        "build_ms": build_ms,
+        "table": {kk: info_t[kk] for kk in ("filter", "filter_log2_bits", "warps", "tile_bytes",
+                                             "stages", "ctas_per_sm", "smem_bytes", "sm_count")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "scan_kernel", "peak_source": f"{peak_src} hbm_gbs",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n,
+                "d2h_bytes_per_step": 16 + 8 * m},
+        "gpu_launches": args.steps * (1 + sort_launches(n, k)),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * rk.h - C ABI of a multi-pattern Rabin-Karp matcher for one GB300 GPU.
+ *
+ * Problem (Shah & Oza, "Improved Parallel Rabin-Karp Algorithm Using CUDA",
+ * Section 1): find every occurrence of every pattern of a set in a byte text.
+ * The result is the set of matches
+ *
+ *     { (id, x) : 0 <= id < k, 0 <= x <= n - len_id, T[x .. x+len_id) == P_id }
+ *
+ * with one window per text offset x (Section 3.1; the GPU listing's bound
+ * x <= n - m, so the last window counts), bytes compared as unsigned values,
+ * every pattern index reported on its own (duplicate patterns included), and
+ * the list returned in ascending (id, x) order.
+ *
+ * Each match is one 64-bit key  key = (id << 40) | x  (RK_KEY below), so the
+ * ascending key order is the ascending (id, x) order.
+ *
+ * Conventions for every entry point:
+ *   - the return value is an RK_* status code; nothing aborts, throws or traps;
+ *   - "d_" pointers are device pointers on the table's device, "h_" pointers
+ *     host pointers; the caller owns every buffer it passes in;
+ *   - the library owns rk_table objects (rk_build / rk_destroy);
+ *   - a table is read-only after rk_build and may serve concurrent searches on
+ *     different streams, except rk_search (host buffers), which serialises
+ *     calls on one table;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); *_device calls are asynchronous with respect to the host;
+ *   - the current CUDA device must be the table's device (else RK_EINVAL).
+ */
+#ifndef RK_H
+#define RK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RK_OK 0
+#define RK_EINVAL 1      /* bad argument (null pointer, size or limit out of range) */
+#define RK_ENOMEM 2      /* a host or device allocation failed */
+#define RK_ECAPACITY 3   /* more matches than the output can hold; count reported */
+#define RK_ECUDA 4       /* a CUDA runtime call or kernel launch failed */
+#define RK_ETIMEOUT 5    /* a bounded device-side wait gave up (pipeline stalled) */
+
+/* ---- limits ------------------------------------------------------------ */
+#define RK_MAX_PATTERN_LEN 4096u            /* bytes per pattern */
+#define RK_MAX_PATTERNS ((1u << 24) - 1u)   /* patterns per table */
+#define RK_MAX_TEXT_LEN ((1ull << 40) - 1u) /* bytes per text */
+
+/* ---- match keys -------------------------------------------------------- */
+#define RK_KEY_OFFSET_BITS 40
+#define RK_KEY(id, x) ((((uint64_t)(id)) << RK_KEY_OFFSET_BITS) | (uint64_t)(x))
+#define RK_KEY_ID(key) ((uint32_t)((key) >> RK_KEY_OFFSET_BITS))
+#define RK_KEY_OFFSET(key) ((uint64_t)(key) & ((1ull << RK_KEY_OFFSET_BITS) - 1u))
+
+/* ---- device result header ---------------------------------------------- */
+/* d_info points to two uint64_t in device memory:
+ *   d_info[0]  number of matches found (may exceed the capacity passed in);
+ *   d_info[1]  RK_OK, or RK_ETIMEOUT if a bounded device wait gave up.       */
+#define RK_INFO_COUNT 0
+#define RK_INFO_STATUS 1
+
+/* ---- stage-1 prefilter choice (see rk_build_opts.filter) ---------------- */
+#define RK_FILTER_AUTO 0        /* pick by pattern count (default) */
+#define RK_FILTER_REPLICATED 1  /* bit set copied into all 32 shared-memory banks */
+#define RK_FILTER_FLAT 2        /* one larger bit set */
+#define RK_FILTER_NONE 3        /* no prefilter: every window hashed at every length */
+
+typedef struct rk_table rk_table;
+
+/* Build options; a zero field means "default".  Pass NULL for all defaults. */
+typedef struct rk_build_opts {
+    uint32_t base_log2;        /* Rabin base B = 2^base_log2, 1..60 (default 8, B = 256);
+                                  1 is the paper's shift-add base 2 */
+    uint32_t filter;           /* RK_FILTER_* */
+    uint32_t filter_log2_bits; /* prefilter size in bits, log2 (default: by pattern count) */
+    uint32_t warps;            /* consumer warps per CTA, 1..32 (default 16) */
+    uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16 (default 32768) */
+    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 3) */
+    uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
+} rk_build_opts;
+
+/* Read-back of a table's shape and launch configuration. */
+typedef struct rk_table_info {
+    uint32_t n_patterns, min_len, max_len, n_lengths;
+    uint32_t gram_len;         /* q: bytes of the stage-1 key (min(4, min_len)) */
+    uint32_t base_log2;
+    uint32_t filter, filter_log2_bits, filter_smem_bytes;
+    uint32_t n_grams;          /* distinct q-byte pattern prefixes */
+    uint32_t warps, tile_bytes, stages, ctas_per_sm, halo_bytes, smem_bytes;
+    uint32_t sm_count;
+    uint32_t device;
+    uint64_t device_bytes;     /* device memory held by the table */
+} rk_table_info;
+
+/* Human-readable text of a status code (static storage). */
+const char *rk_strerror(int status);
+
+/* Build the pattern table (Section 3.1: the pattern hash is computed once on
+ * the host and handed to the kernel; here one table serves a whole set).
+ *   patterns   all pattern bytes concatenated (pattern i follows pattern i-1);
+ *   lens       n_patterns lengths, each 1..RK_MAX_PATTERN_LEN;
+ *   n_patterns 0..RK_MAX_PATTERNS (0 gives a table that never matches);
+ *   opts       NULL or options; *out receives the table.
+ * Pattern ids are the indices 0..n_patterns-1.  The bytes are copied; the
+ * table lives in device memory of the current device until rk_destroy.
+ * Errors: RK_EINVAL (null pointer, empty or overlong pattern, bad option),
+ * RK_ENOMEM, RK_ECUDA.  On error *out is set to NULL.                        */
+int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t n_patterns,
+             const rk_build_opts *opts, rk_table **out);
+
+/* Free a table (NULL is ignored).  No search may be in flight on it. */
+void rk_destroy(rk_table *t);
+
+int rk_table_info_get(const rk_table *t, rk_table_info *info);
+
+/* Bytes of device workspace rk_sort_device / rk_search_device need for an
+ * output of `capacity` keys (0 on bad arguments). */
+uint64_t rk_workspace_bytes(const rk_table *t, uint64_t capacity);
+
+/* Scan (Section 3.1 GPU listing, rebuilt: staged tiles, per-window Rabin
+ * hashes mod 2^61-1, probes of tables grouped by pattern length, byte-exact
+ * verification, warp-aggregated emission).  Appends the unsorted keys of all
+ * matches in d_text[0..n) to d_keys[0..capacity) and sets d_info.
+ *   d_text     n bytes of device memory, any alignment; n <= RK_MAX_TEXT_LEN;
+ *   d_keys     capacity uint64_t of device memory, 8-byte aligned;
+ *   d_info     2 uint64_t of device memory (zeroed by this call).
+ * If d_info[0] > capacity, only `capacity` keys were stored (which ones is
+ * unspecified): retry with a larger buffer.  Errors: RK_EINVAL, RK_ECUDA.    */
+int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
+                   uint64_t capacity, uint64_t *d_info, void *stream);
+
+/* Sort the keys left by rk_scan_device ascending (= ascending (id, x)), in
+ * place, reading the count from d_info on the device.  Does nothing when
+ * d_info[0] > capacity.  n must be the text length given to the scan.
+ *   d_workspace  at least rk_workspace_bytes(t, capacity) bytes, 16-byte aligned.
+ * Errors: RK_EINVAL, RK_ECUDA.                                               */
+int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
+                   const uint64_t *d_info, void *d_workspace, uint64_t workspace_bytes,
+                   void *stream);
+
+/* rk_scan_device followed by rk_sort_device on one stream: the sorted match
+ * list of d_text[0..n) in d_keys, its length in d_info[0].                   */
+int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
+                     uint64_t capacity, uint64_t *d_info, void *d_workspace,
+                     uint64_t workspace_bytes, void *stream);
+
+/* Host-buffer search: copies h_text to the device in chunks (overlapping the
+ * copies with the scan), sorts, and copies the sorted keys back.  Blocks until
+ * done.  *n_matches receives the match count; if it exceeds capacity the call
+ * returns RK_ECAPACITY and h_keys is left untouched.  Device buffers are cached
+ * on the table between calls and freed by rk_destroy.
+ * Errors: RK_EINVAL, RK_ENOMEM, RK_ECAPACITY, RK_ECUDA, RK_ETIMEOUT.         */
+int rk_search(const rk_table *t, const uint8_t *h_text, uint64_t n, uint64_t *h_keys,
+              uint64_t capacity, uint64_t *n_matches);
+
+/* Rabin hash of every length-L window (Section 3.1's hash h = h*B + c,
+ * reduced mod 2^61-1, B = 2^base_log2), by a tiled rolling update:
+ *   d_hashes[x] = sum_{i<L} d_text[x+i] * B^(L-1-i)  mod (2^61 - 1),
+ *   x = 0 .. n-L  (nothing is written when L > n).
+ * L in 1..RK_MAX_PATTERN_LEN, base_log2 in 1..60.  Errors: RK_EINVAL, RK_ECUDA. */
+int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint32_t base_log2,
+                            uint64_t *d_hashes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RK_H */

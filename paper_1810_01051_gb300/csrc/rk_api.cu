@@ -1,0 +1,199 @@
+// Public entry points of rk.h: device-buffer scan / sort / search, the
+// host-buffer search with copy/scan overlap, and the per-window hash kernel.
+#include <algorithm>
+
+#include "rk_internal.cuh"
+
+using namespace rk;
+
+namespace {
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int scan_args_ok(const rk_table *t, const uint8_t *d_text, uint64_t n, const uint64_t *d_keys,
+                 uint64_t capacity, const uint64_t *d_info) {
+    if (!t || !d_info || !aligned(d_info, 8)) return RK_EINVAL;
+    if (n > RK_MAX_TEXT_LEN || (n && !d_text)) return RK_EINVAL;
+    if (capacity && (!d_keys || !aligned(d_keys, 8))) return RK_EINVAL;
+    if (capacity >= (1ull << 32)) return RK_EINVAL;
+    return check_device(t);
+}
+
+// ---- A2 on its own: Rabin hash of every window by a tiled rolling update --
+constexpr uint32_t kRollRun = 64;  // windows per thread
+
+__global__ void window_hash_kernel(const uint8_t *text, uint64_t n, uint32_t L, uint32_t k,
+                                   uint64_t *out) {
+    const uint64_t nw = n - L + 1;
+    const uint32_t s_out = (uint32_t)((uint64_t)k * (L - 1) % 61);  // B^(L-1) = 2^s_out
+    for (uint64_t run = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; run * kRollRun < nw;
+         run += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x0 = run * kRollRun;
+        const uint64_t x1 = min(nw, x0 + kRollRun);
+        uint64_t h = 0;
+        for (uint32_t i = 0; i < L; ++i) {
+            h = rotl61(h, k) + text[x0 + i];
+            if (h >= kP61) h -= kP61;
+        }
+        out[x0] = h;
+        for (uint64_t x = x0; x + 1 < x1; ++x) {
+            // h(x+1) = (h(x) - T[x] * B^(L-1)) * B + T[x+L]
+            uint64_t outgoing = s_out ? rotl61((uint64_t)text[x], s_out) : (uint64_t)text[x];
+            h = submod61(h, outgoing);
+            h = rotl61(h, k) + text[x + L];
+            if (h >= kP61) h -= kP61;
+            out[x + 1] = h;
+        }
+    }
+}
+
+int ensure(void **p, uint64_t *cap, uint64_t need) {
+    if (*cap >= need && *p) return RK_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return RK_ENOMEM;
+    }
+    *cap = need;
+    return RK_OK;
+}
+
+}  // namespace
+
+extern "C" uint64_t rk_workspace_bytes(const rk_table *t, uint64_t capacity) {
+    if (!t) return 0;
+    return sort_workspace_bytes(capacity);
+}
+
+extern "C" int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                              uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                              void *stream) {
+    int rc = scan_args_ok(t, d_text, n, d_keys, capacity, d_info);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_info, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return RK_ECUDA;
+    return launch_scan(t, d_text, n, 0, n, d_keys, capacity, d_info, st);
+}
+
+extern "C" int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
+                              const uint64_t *d_info, void *d_workspace, uint64_t workspace_bytes,
+                              void *stream) {
+    if (!t || !d_info || !aligned(d_info, 8) || n > RK_MAX_TEXT_LEN) return RK_EINVAL;
+    if (capacity >= (1ull << 32)) return RK_EINVAL;
+    if (capacity && (!d_keys || !aligned(d_keys, 8))) return RK_EINVAL;
+    if (capacity >= 2 && (!d_workspace || !aligned(d_workspace, 16) ||
+                          workspace_bytes < sort_workspace_bytes(capacity)))
+        return RK_EINVAL;
+    int rc = check_device(t);
+    if (rc) return rc;
+    return launch_sort(t, n, d_keys, capacity, d_info, d_workspace, workspace_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                                uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                                void *d_workspace, uint64_t workspace_bytes, void *stream) {
+    int rc = scan_args_ok(t, d_text, n, d_keys, capacity, d_info);
+    if (rc) return rc;
+    if (capacity >= 2 && (!d_workspace || !aligned(d_workspace, 16) ||
+                          workspace_bytes < sort_workspace_bytes(capacity)))
+        return RK_EINVAL;
+    rc = rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
+    if (rc) return rc;
+    return launch_sort(t, n, d_keys, capacity, d_info, d_workspace, workspace_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rk_search(const rk_table *tc, const uint8_t *h_text, uint64_t n, uint64_t *h_keys,
+                         uint64_t capacity, uint64_t *n_matches) {
+    if (!tc || !n_matches || n > RK_MAX_TEXT_LEN || (n && !h_text) || (capacity && !h_keys))
+        return RK_EINVAL;
+    if (capacity >= (1ull << 32)) return RK_EINVAL;
+    int rc = check_device(tc);
+    if (rc) return rc;
+    rk_table *t = const_cast<rk_table *>(tc);  // only the host-path cache is mutated
+    std::lock_guard<std::mutex> lock(t->host_mu);
+    *n_matches = 0;
+
+    if (!t->s_copy && cudaStreamCreateWithFlags(&t->s_copy, cudaStreamNonBlocking) != cudaSuccess)
+        return RK_ECUDA;
+    if (!t->s_comp && cudaStreamCreateWithFlags(&t->s_comp, cudaStreamNonBlocking) != cudaSuccess)
+        return RK_ECUDA;
+    if ((rc = ensure(reinterpret_cast<void **>(&t->h_text), &t->h_text_cap, std::max<uint64_t>(n, 16))))
+        return rc;
+    uint64_t kcap = std::max<uint64_t>(capacity, 2);
+    uint64_t cap_bytes = t->h_keys_cap;
+    if ((rc = ensure(reinterpret_cast<void **>(&t->h_keys), &cap_bytes, kcap * 8))) return rc;
+    t->h_keys_cap = cap_bytes;
+    uint64_t info_cap = t->h_info ? 16 : 0;
+    if ((rc = ensure(reinterpret_cast<void **>(&t->h_info), &info_cap, 16))) return rc;
+    if ((rc = ensure(&t->h_ws, &t->h_ws_cap, sort_workspace_bytes(kcap)))) return rc;
+
+    // Copy the text in chunks on one stream while the other scans the windows
+    // whose bytes (window + longest pattern - 1) have arrived.
+    const uint64_t chunk = 64ull << 20;
+    const uint64_t nchunks = n ? (n + chunk - 1) / chunk : 0;
+    while (t->events.size() < nchunks) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return RK_ECUDA;
+        t->events.push_back(e);
+    }
+    cudaStream_t sc = t->s_comp, sx = t->s_copy;
+    bool ok = cudaMemsetAsync(t->h_info, 0, 16, sc) == cudaSuccess;
+    for (uint64_t c = 0; ok && c < nchunks; ++c) {
+        uint64_t b = c * chunk, e = std::min(n, b + chunk);
+        ok = cudaMemcpyAsync(t->h_text + b, h_text + b, e - b, cudaMemcpyHostToDevice, sx) ==
+                 cudaSuccess &&
+             cudaEventRecord(t->events[c], sx) == cudaSuccess;
+    }
+    const uint64_t reach = t->dev.lmax ? t->dev.lmax - 1 : 0;
+    for (uint64_t c = 0; ok && c < nchunks; ++c) {
+        uint64_t b = c * chunk, e = std::min(n, b + chunk);
+        uint64_t need = std::min(n, e + reach);                  // last byte a window may read
+        uint64_t last = need ? (need - 1) / chunk : 0;          // chunk holding it
+        ok = cudaStreamWaitEvent(sc, t->events[last], 0) == cudaSuccess;
+        if (ok && launch_scan(t, t->h_text, n, b, e, t->h_keys, capacity, t->h_info, sc) != RK_OK)
+            ok = false;
+    }
+    if (!ok) {
+        cudaStreamSynchronize(sx);
+        cudaStreamSynchronize(sc);
+        return RK_ECUDA;
+    }
+    if (capacity >= 2 &&
+        launch_sort(t, n, t->h_keys, capacity, t->h_info, t->h_ws, t->h_ws_cap, sc) != RK_OK)
+        return RK_ECUDA;
+    uint64_t info[2] = {0, 0};
+    if (cudaMemcpyAsync(info, t->h_info, 16, cudaMemcpyDeviceToHost, sc) != cudaSuccess ||
+        cudaStreamSynchronize(sc) != cudaSuccess)
+        return RK_ECUDA;
+    *n_matches = info[0];
+    if (info[1] != RK_OK) return (int)info[1];
+    if (info[0] > capacity) return RK_ECAPACITY;
+    if (info[0] && (cudaMemcpyAsync(h_keys, t->h_keys, info[0] * 8, cudaMemcpyDeviceToHost, sc) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(sc) != cudaSuccess))
+        return RK_ECUDA;
+    return RK_OK;
+}
+
+extern "C" int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L,
+                                       uint32_t base_log2, uint64_t *d_hashes, void *stream) {
+    if (L < 1 || L > RK_MAX_PATTERN_LEN || base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
+    if (n > RK_MAX_TEXT_LEN) return RK_EINVAL;
+    if (L > n) return RK_OK;
+    if (!d_text || !d_hashes || !aligned(d_hashes, 8)) return RK_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RK_ECUDA;
+    uint64_t runs = (n - L + 1 + kRollRun - 1) / kRollRun;
+    uint64_t blocks = std::min<uint64_t>((runs + 255) / 256, (uint64_t)sms * 8);
+    window_hash_kernel<<<(uint32_t)std::max<uint64_t>(blocks, 1), 256, 0,
+                         reinterpret_cast<cudaStream_t>(stream)>>>(d_text, n, L, base_log2,
+                                                                     d_hashes);
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}

@@ -1,0 +1,221 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "rk.h"
+
+namespace rk {
+
+// Mersenne prime modulus of the Rabin hash: p = 2^61 - 1.
+constexpr uint64_t kP61 = (1ull << 61) - 1;
+
+// Multipliers of the multiplicative hashes that place keys in tables.
+constexpr uint32_t kFilterMult = 0x85EBCA77u;
+constexpr uint32_t kGramMult = 0x9E3779B1u;
+constexpr uint64_t kGroupMult = 0x9E3779B97F4A7C15ull;
+
+enum FilterMode : uint32_t { kFilterNone = 0, kFilterReplicated = 1, kFilterFlat = 2 };
+
+// One slot of a length group's hash table: the Rabin hash of some patterns of
+// that length and the run [first, first+count) of their ids in group_pids.
+struct GroupSlot {
+    uint64_t h;
+    uint32_t first;
+    uint32_t count;  // 0 = empty slot
+};
+
+// One slot of the prefix map: a q-byte pattern prefix (big-endian value) and
+// the run [first, first+count) of distinct pattern lengths in gram_lens.
+struct GramSlot {
+    uint32_t key;
+    uint32_t first;
+    uint32_t count;  // 0 = empty slot
+    uint32_t pad;
+};
+
+// Device view of a table (pointers into one device allocation), passed to the
+// scan kernel by value.
+struct DevTable {
+    const uint32_t *filter;   // shared-memory image of the stage-1 bit set
+    uint32_t filter_bytes;    // bytes of that image
+    uint32_t filter_mode;     // FilterMode
+    uint32_t filter_mask;     // address mask (see scan kernel)
+    uint32_t q;               // stage-1 key length in bytes, 1..4
+
+    const GramSlot *grams;    // prefix map, 2^gram_bits slots
+    uint32_t gram_bits;
+    const uint32_t *gram_lens;
+
+    const uint2 *group_hdr;   // per length L = 0..lmax: {first slot, log2 slots}; .y == 0: none
+    const GroupSlot *slots;
+    const uint32_t *group_pids;
+
+    const uint8_t *pbytes;    // pattern bytes, each pattern 8-byte aligned, zero padded
+    const uint64_t *poff;     // byte offset of each pattern in pbytes
+    const uint32_t *plen;
+    const uint32_t *lengths;  // distinct lengths, ascending
+    uint32_t n_lengths;
+
+    uint32_t n_patterns;
+    uint32_t lmin, lmax;
+    uint32_t base_log2;
+};
+
+struct Tuning {
+    uint32_t warps;        // consumer warps per CTA
+    uint32_t tile_bytes;
+    uint32_t stages;
+    uint32_t ctas_per_sm;
+    uint32_t halo;         // bytes staged after each tile (multiple of 16, >= 16)
+    uint32_t smem_bytes;   // dynamic shared memory per CTA
+};
+
+}  // namespace rk
+
+// Host object behind the opaque handle.
+struct rk_table {
+    int device = 0;
+    int sm_count = 0;
+    rk::DevTable dev{};
+    rk::Tuning tune{};
+    uint32_t n_grams = 0;
+    uint32_t filter_log2_bits = 0;
+    uint32_t filter_opt = RK_FILTER_AUTO;
+    void *d_mem = nullptr;
+    size_t d_bytes = 0;
+
+    // Buffers of the host-buffer search path, grown on demand.
+    std::mutex host_mu;
+    uint8_t *h_text = nullptr;  // device text buffer
+    uint64_t h_text_cap = 0;
+    uint64_t *h_keys = nullptr;
+    uint64_t h_keys_cap = 0;
+    uint64_t *h_info = nullptr;
+    void *h_ws = nullptr;
+    uint64_t h_ws_cap = 0;
+    cudaStream_t s_copy = nullptr, s_comp = nullptr;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace rk {
+
+// Scan windows whose start x lies in [x_begin, x_end) of a text of n bytes
+// (bytes up to min(n, x_end + lmax - 1) must be resident); adds to d_info.
+int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
+                uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                cudaStream_t stream);
+
+int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
+                const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);
+
+uint64_t sort_workspace_bytes(uint64_t capacity);
+
+int check_device(const rk_table *t);
+
+}  // namespace rk
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace rk {
+
+// 61-bit rotation: x * 2^s mod p for x < p, 0 < s < 61 (2^61 = 1 mod p).
+__device__ __forceinline__ uint64_t rotl61(uint64_t x, uint32_t s) {
+    return ((x << s) | (x >> (61 - s))) & kP61;
+}
+
+// x mod p for any 64-bit x (one fold leaves at most p + 7).
+__device__ __forceinline__ uint64_t fold61(uint64_t x) {
+    uint64_t r = (x & kP61) + (x >> 61);
+    return r >= kP61 ? r - kP61 : r;
+}
+
+__device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b) {  // a, b < p
+    uint64_t s = a + b;
+    return s >= kP61 ? s - kP61 : s;
+}
+
+__device__ __forceinline__ uint64_t submod61(uint64_t a, uint64_t b) {  // a, b < p
+    return a >= b ? a - b : a + kP61 - b;
+}
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0, 0x0123);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- mbarrier / bulk-copy wrappers (PTX ISA, sm_90+) ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make initialised barriers visible to the bulk-copy (async) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete, for at most
+// timeout_ns of wall-clock time.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > timeout_ns) return false;
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared (no tensor map, no multicast); completion
+// is signalled on `bar` as transaction bytes.  dst, src 16-byte aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace rk
+#endif  // __CUDACC__

@@ -1,0 +1,47 @@
+// Shared-memory layout of the scan kernel, computed identically on host
+// (launch size) and device (carving the dynamic shared memory).
+#pragma once
+
+#include <stdint.h>
+
+namespace rk {
+
+constexpr uint32_t kQueueCap = 64;    // stage-1 survivor entries per warp
+constexpr uint32_t kMatchCap = 128;   // buffered match keys per warp
+constexpr uint32_t kStagePad = 16;    // readable slack after each staged tile
+
+struct SmemLayout {
+    uint32_t filter_off, bar_off, queue_off, qcount_off, mcount_off, match_off, stage_off;
+    uint32_t stage_stride;
+    uint32_t total;
+};
+
+__host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) {
+    return (x + a - 1) / a * a;
+}
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t filter_bytes, uint32_t warps,
+                                                  uint32_t stages, uint32_t tile_bytes,
+                                                  uint32_t halo) {
+    SmemLayout L{};
+    uint32_t off = 0;
+    L.filter_off = off;
+    off = align_up(off + filter_bytes, 128);
+    L.bar_off = off;
+    off = align_up(off + 2 * stages * 8, 16);
+    L.queue_off = off;
+    off = align_up(off + warps * kQueueCap * 4, 16);
+    L.qcount_off = off;
+    off = align_up(off + warps * 4, 16);
+    L.mcount_off = off;
+    off = align_up(off + warps * 4, 16);
+    L.match_off = off;
+    off = align_up(off + warps * kMatchCap * 8, 128);
+    L.stage_off = off;
+    L.stage_stride = align_up(tile_bytes + halo + kStagePad, 128);
+    off += stages * L.stage_stride;
+    L.total = off;
+    return L;
+}
+
+}  // namespace rk

@@ -1,0 +1,361 @@
+// Pattern-table builder (host side of rk_build) and table bookkeeping.
+//
+// Section 3.1 computes the pattern hash once on the host and passes it to the
+// kernel.  For a pattern set the host builds, in one device allocation:
+//   - stage-1 bit set over the q-byte prefixes of all patterns (q = min(4,
+//     shortest length)), keyed by the prefix's big-endian value (its Rabin
+//     hash for B = 256, exact because 256^q < 2^61 - 1);
+//   - prefix map: exact q-byte prefix -> distinct lengths of the patterns
+//     that start with it;
+//   - one open-addressing table per pattern length L, keyed by the Rabin
+//     hash h_B(P) = sum_i P[i] * B^(L-1-i) mod (2^61 - 1), B = 2^base_log2,
+//     each slot naming the ids of the patterns of that length and hash;
+//   - the pattern bytes, each pattern 8-byte aligned and zero padded.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <utility>
+
+#include "rk_internal.cuh"
+#include "rk_layout.cuh"
+
+namespace rk {
+namespace {
+
+uint64_t host_rotl61(uint64_t x, uint32_t s) { return ((x << s) | (x >> (61 - s))) & kP61; }
+
+// Rabin hash mod 2^61-1 with B = 2^k: Horner's rule, multiplication by B
+// being a 61-bit rotation by k.
+uint64_t host_rabin(const uint8_t *s, uint32_t L, uint32_t k) {
+    uint64_t h = 0;
+    for (uint32_t i = 0; i < L; ++i) {
+        h = host_rotl61(h, k) + s[i];
+        if (h >= kP61) h -= kP61;
+    }
+    return h;
+}
+
+uint32_t ceil_log2(uint64_t x) {
+    uint32_t b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+uint32_t prefix_key(const uint8_t *s, uint32_t q) {
+    uint32_t v = 0;
+    for (uint32_t i = 0; i < q; ++i) v = (v << 8) | s[i];
+    return v;
+}
+
+struct Blob {  // host staging of the device allocation
+    std::vector<uint8_t> bytes;
+    size_t add(size_t n, size_t align = 256) {
+        size_t off = (bytes.size() + align - 1) / align * align;
+        bytes.resize(off + n);
+        return off;
+    }
+};
+
+}  // namespace
+
+int check_device(const rk_table *t) {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return RK_ECUDA;
+    return d == t->device ? RK_OK : RK_EINVAL;
+}
+
+}  // namespace rk
+
+using namespace rk;
+
+extern "C" const char *rk_strerror(int status) {
+    switch (status) {
+        case RK_OK: return "ok";
+        case RK_EINVAL: return "invalid argument";
+        case RK_ENOMEM: return "out of memory";
+        case RK_ECAPACITY: return "output capacity too small";
+        case RK_ECUDA: return "CUDA error";
+        case RK_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
+                        const rk_build_opts *opts, rk_table **out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    if (k > RK_MAX_PATTERNS) return RK_EINVAL;
+    if (k > 0 && (!patterns || !lens)) return RK_EINVAL;
+    rk_build_opts o{};
+    if (opts) o = *opts;
+    uint32_t base_log2 = o.base_log2 ? o.base_log2 : 8;
+    if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
+    if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
+    uint32_t warps = o.warps ? o.warps : 16;
+    uint32_t tile = o.tile_bytes ? o.tile_bytes : 32768;
+    uint32_t stages = o.stages ? o.stages : 3;
+    uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
+    // tile + halo is one bulk copy; an mbarrier phase counts < 2^20 transaction bytes
+    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > (1u << 19) ||
+        stages < 2 || stages > 8 || cps < 1 || cps > 8)
+        return RK_EINVAL;
+
+    // ---- patterns ---------------------------------------------------------
+    std::vector<uint64_t> src_off(k), poff(k);
+    std::vector<uint32_t> plen(k);
+    uint64_t acc = 0, packed = 0;
+    uint32_t lmin = UINT32_MAX, lmax = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+        uint32_t L = lens[i];
+        if (L < 1 || L > RK_MAX_PATTERN_LEN) return RK_EINVAL;
+        src_off[i] = acc;
+        acc += L;
+        plen[i] = L;
+        poff[i] = packed;
+        packed += (L + 7) / 8 * 8;
+        lmin = std::min(lmin, L);
+        lmax = std::max(lmax, L);
+    }
+    if (k == 0) { lmin = 1; lmax = 1; }
+    uint32_t q = std::min<uint32_t>(4, lmin);
+
+    std::vector<uint32_t> lengths(plen);
+    std::sort(lengths.begin(), lengths.end());
+    lengths.erase(std::unique(lengths.begin(), lengths.end()), lengths.end());
+
+    // ---- prefix map: q-byte prefix -> distinct lengths ----------------------
+    std::unordered_map<uint32_t, std::vector<uint32_t>> gram_to_lens;
+    gram_to_lens.reserve(k * 2 + 1);
+    for (uint32_t i = 0; i < k; ++i)
+        gram_to_lens[prefix_key(patterns + src_off[i], q)].push_back(plen[i]);
+    std::vector<uint32_t> gram_keys;
+    gram_keys.reserve(gram_to_lens.size());
+    for (auto &kv : gram_to_lens) {
+        auto &v = kv.second;
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        gram_keys.push_back(kv.first);
+    }
+    std::sort(gram_keys.begin(), gram_keys.end());  // deterministic layout
+    uint32_t D = (uint32_t)gram_keys.size();
+    uint32_t gram_bits = std::max<uint32_t>(4, ceil_log2(2ull * D));
+    std::vector<GramSlot> grams(1ull << gram_bits, GramSlot{0, 0, 0, 0});
+    std::vector<uint32_t> gram_lens;
+    for (uint32_t key : gram_keys) {
+        const auto &v = gram_to_lens[key];
+        uint32_t idx = (key * kGramMult) >> (32 - gram_bits);
+        uint32_t mask = (1u << gram_bits) - 1;
+        while (grams[idx].count) idx = (idx + 1) & mask;
+        grams[idx] = GramSlot{key, (uint32_t)gram_lens.size(), (uint32_t)v.size(), 0};
+        gram_lens.insert(gram_lens.end(), v.begin(), v.end());
+    }
+
+    // ---- stage-1 bit set ---------------------------------------------------
+    uint32_t mode, fbits = o.filter_log2_bits;
+    if (o.filter == RK_FILTER_NONE) {
+        mode = kFilterNone;
+    } else if (o.filter == RK_FILTER_REPLICATED ||
+               (o.filter == RK_FILTER_AUTO && D <= 256 && !fbits)) {
+        mode = kFilterReplicated;
+        if (!fbits) fbits = 14;
+        if (fbits < 10 || fbits > 15) return RK_EINVAL;
+    } else {
+        mode = kFilterFlat;
+        if (!fbits) fbits = std::min<uint32_t>(20, std::max<uint32_t>(15, ceil_log2(64ull * D)));
+        if (fbits < 10 || fbits > 20) return RK_EINVAL;
+    }
+    std::vector<uint32_t> fimg;
+    uint32_t fmask = 0;
+    if (mode != kFilterNone) {
+        uint32_t W = 1u << (fbits - 5);
+        std::vector<uint32_t> bm(W, 0);
+        for (uint32_t key : gram_keys) {
+            uint32_t hi = (uint32_t)(((uint64_t)key * kFilterMult) >> 32);
+            uint32_t word = (mode == kFilterReplicated ? (hi >> 7) : (hi >> 5)) & (W - 1);
+            uint32_t r = hi & 31;
+            // stored one place below r: a right rotation by r moves it to bit 31
+            bm[word] |= 1u << ((r + 31) & 31);
+        }
+        if (mode == kFilterReplicated) {
+            fimg.resize((size_t)W * 32);
+            for (uint32_t w = 0; w < W; ++w)
+                for (uint32_t l = 0; l < 32; ++l) fimg[(size_t)w * 32 + l] = bm[w];
+            fmask = (W - 1) << 7;
+        } else {
+            fimg = bm;
+            fmask = (W - 1) << 2;
+        }
+    }
+
+    // ---- per-length hash tables -------------------------------------------
+    std::vector<uint2> group_hdr(lmax + 1, make_uint2(0, 0));
+    std::vector<GroupSlot> slots;
+    std::vector<uint32_t> group_pids;
+    group_pids.reserve(k);
+    {
+        std::vector<std::vector<uint32_t>> by_len(lmax + 1);
+        for (uint32_t i = 0; i < k; ++i) by_len[plen[i]].push_back(i);
+        for (uint32_t L : lengths) {
+            auto &ids = by_len[L];
+            std::vector<std::pair<uint64_t, uint32_t>> hp;
+            hp.reserve(ids.size());
+            for (uint32_t id : ids) hp.emplace_back(host_rabin(patterns + src_off[id], L, base_log2), id);
+            std::sort(hp.begin(), hp.end());
+            uint32_t uniq = 0;
+            for (size_t i = 0; i < hp.size(); ++i)
+                if (i == 0 || hp[i].first != hp[i - 1].first) ++uniq;
+            uint32_t bits = std::max<uint32_t>(1, ceil_log2(2ull * uniq));
+            uint32_t first_slot = (uint32_t)slots.size();
+            slots.resize(slots.size() + (1ull << bits), GroupSlot{0, 0, 0});
+            group_hdr[L] = make_uint2(first_slot, bits);
+            uint64_t mask = (1ull << bits) - 1;
+            for (size_t i = 0; i < hp.size();) {
+                size_t j = i;
+                while (j < hp.size() && hp[j].first == hp[i].first) ++j;
+                uint64_t h = hp[i].first;
+                uint64_t idx = (h * kGroupMult) >> (64 - bits);
+                while (slots[first_slot + idx].count) idx = (idx + 1) & mask;
+                slots[first_slot + idx] = GroupSlot{h, (uint32_t)group_pids.size(), (uint32_t)(j - i)};
+                for (size_t m = i; m < j; ++m) group_pids.push_back(hp[m].second);
+                i = j;
+            }
+        }
+    }
+
+    // ---- one device allocation --------------------------------------------
+    Blob b;
+    size_t o_filter = b.add(fimg.size() * 4 + 16);
+    size_t o_grams = b.add(grams.size() * sizeof(GramSlot));
+    size_t o_glens = b.add(gram_lens.size() * 4 + 4);
+    size_t o_ghdr = b.add(group_hdr.size() * sizeof(uint2));
+    size_t o_slots = b.add(slots.size() * sizeof(GroupSlot) + sizeof(GroupSlot));
+    size_t o_gpids = b.add(group_pids.size() * 4 + 4);
+    size_t o_pbytes = b.add(packed + 16);
+    size_t o_poff = b.add(k * 8 + 8);
+    size_t o_plen = b.add(k * 4 + 4);
+    size_t o_lens = b.add(lengths.size() * 4 + 4);
+    uint8_t *hb = b.bytes.data();
+    if (!fimg.empty()) memcpy(hb + o_filter, fimg.data(), fimg.size() * 4);
+    memcpy(hb + o_grams, grams.data(), grams.size() * sizeof(GramSlot));
+    if (!gram_lens.empty()) memcpy(hb + o_glens, gram_lens.data(), gram_lens.size() * 4);
+    memcpy(hb + o_ghdr, group_hdr.data(), group_hdr.size() * sizeof(uint2));
+    if (!slots.empty()) memcpy(hb + o_slots, slots.data(), slots.size() * sizeof(GroupSlot));
+    if (!group_pids.empty()) memcpy(hb + o_gpids, group_pids.data(), group_pids.size() * 4);
+    for (uint32_t i = 0; i < k; ++i) memcpy(hb + o_pbytes + poff[i], patterns + src_off[i], plen[i]);
+    if (k) memcpy(hb + o_poff, poff.data(), k * 8);
+    if (k) memcpy(hb + o_plen, plen.data(), k * 4);
+    if (!lengths.empty()) memcpy(hb + o_lens, lengths.data(), lengths.size() * 4);
+
+    int dev = 0, sms = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RK_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RK_ECUDA;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+        return RK_ECUDA;
+
+    // ---- launch shape: shrink stages / tile until shared memory fits -------
+    uint32_t halo = align_up(std::max<uint32_t>(lmax - 1, 1), 16);
+    uint32_t fbytes = (uint32_t)(fimg.size() * 4);
+    uint32_t limit = (uint32_t)smem_optin / cps - 1024;  // room for static shared memory
+    SmemLayout lay = smem_layout(fbytes, warps, stages, tile, halo);
+    while (lay.total > limit) {
+        if (stages > 2) --stages;
+        else if (tile > 4 * halo && tile > 4096) tile /= 2;
+        else return RK_EINVAL;
+        tile = tile / 16 * 16;
+        lay = smem_layout(fbytes, warps, stages, tile, halo);
+    }
+
+    rk_table *t = new (std::nothrow) rk_table();
+    if (!t) return RK_ENOMEM;
+    t->device = dev;
+    t->sm_count = sms;
+    if (cudaMalloc(&t->d_mem, b.bytes.size()) != cudaSuccess) {
+        delete t;
+        cudaGetLastError();
+        return RK_ENOMEM;
+    }
+    t->d_bytes = b.bytes.size();
+    if (cudaMemcpy(t->d_mem, hb, b.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->d_mem);
+        delete t;
+        return RK_ECUDA;
+    }
+    uint8_t *dm = (uint8_t *)t->d_mem;
+    DevTable &d = t->dev;
+    d.filter = (const uint32_t *)(dm + o_filter);
+    d.filter_bytes = fbytes;
+    d.filter_mode = mode;
+    d.filter_mask = fmask;
+    d.q = q;
+    d.grams = (const GramSlot *)(dm + o_grams);
+    d.gram_bits = gram_bits;
+    d.gram_lens = (const uint32_t *)(dm + o_glens);
+    d.group_hdr = (const uint2 *)(dm + o_ghdr);
+    d.slots = (const GroupSlot *)(dm + o_slots);
+    d.group_pids = (const uint32_t *)(dm + o_gpids);
+    d.pbytes = dm + o_pbytes;
+    d.poff = (const uint64_t *)(dm + o_poff);
+    d.plen = (const uint32_t *)(dm + o_plen);
+    d.lengths = (const uint32_t *)(dm + o_lens);
+    d.n_lengths = (uint32_t)lengths.size();
+    d.n_patterns = k;
+    d.lmin = lmin;
+    d.lmax = lmax;
+    d.base_log2 = base_log2;
+    t->tune = Tuning{warps, tile, stages, cps, halo, lay.total};
+    t->n_grams = D;
+    t->filter_log2_bits = mode == kFilterNone ? 0 : fbits;
+    t->filter_opt = o.filter;
+    *out = t;
+    return RK_OK;
+}
+
+extern "C" void rk_destroy(rk_table *t) {
+    if (!t) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != t->device) cudaSetDevice(t->device);
+    if (t->s_copy) cudaStreamSynchronize(t->s_copy);
+    if (t->s_comp) cudaStreamSynchronize(t->s_comp);
+    for (cudaEvent_t e : t->events) cudaEventDestroy(e);
+    if (t->s_copy) cudaStreamDestroy(t->s_copy);
+    if (t->s_comp) cudaStreamDestroy(t->s_comp);
+    cudaFree(t->h_text);
+    cudaFree(t->h_keys);
+    cudaFree(t->h_info);
+    cudaFree(t->h_ws);
+    cudaFree(t->d_mem);
+    if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+    delete t;
+}
+
+extern "C" int rk_table_info_get(const rk_table *t, rk_table_info *info) {
+    if (!t || !info) return RK_EINVAL;
+    rk_table_info r{};
+    r.n_patterns = t->dev.n_patterns;
+    r.min_len = t->dev.lmin;
+    r.max_len = t->dev.lmax;
+    r.n_lengths = t->dev.n_lengths;
+    r.gram_len = t->dev.q;
+    r.base_log2 = t->dev.base_log2;
+    r.filter = t->dev.filter_mode == kFilterNone ? RK_FILTER_NONE
+               : t->dev.filter_mode == kFilterReplicated ? RK_FILTER_REPLICATED
+                                                          : RK_FILTER_FLAT;
+    r.filter_log2_bits = t->filter_log2_bits;
+    r.filter_smem_bytes = t->dev.filter_bytes;
+    r.n_grams = t->n_grams;
+    r.warps = t->tune.warps;
+    r.tile_bytes = t->tune.tile_bytes;
+    r.stages = t->tune.stages;
+    r.ctas_per_sm = t->tune.ctas_per_sm;
+    r.halo_bytes = t->tune.halo;
+    r.smem_bytes = t->tune.smem_bytes;
+    r.sm_count = (uint32_t)t->sm_count;
+    r.device = (uint32_t)t->device;
+    r.device_bytes = t->d_bytes;
+    *info = r;
+    return RK_OK;
+}

@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports what include/rk.h declares
+(CPU only: no call here reaches the GPU)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1810_01051_gb300 import build_lib, rk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "rk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rk_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return rk.load()
+
+
+def test_header_declares_binding_exports():
+    assert header_functions() == sorted(rk.EXPORTS)
+
+
+def test_every_declared_symbol_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", build_lib.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (rk_\w+)$", out, flags=re.M))
+    for name in header_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_library_is_for_sm103a(lib):
+    # the fatbinary names its target; cuobjdump only lists the architectures
+    out = subprocess.run(["cuobjdump", "--list-elf", build_lib.LIB], capture_output=True, text=True)
+    assert "sm_103a" in out.stdout, out.stdout + out.stderr
+
+
+def test_strerror(lib):
+    assert rk.strerror(rk.RK_OK) == "ok"
+    assert "capacity" in rk.strerror(rk.RK_ECAPACITY)
+    assert rk.strerror(99) == "unknown status"
+
+
+def _build_raw(lib, pats, lens, opts=None):
+    out = ctypes.c_void_p(123)
+    cat = np.frombuffer(b"".join(pats) or b"\0", dtype=np.uint8).copy()
+    ln = np.array(lens, dtype=np.uint32)
+    rc = lib.rk_build(cat.ctypes.data, ln.ctypes.data, len(lens),
+                      ctypes.byref(opts) if opts else None, ctypes.byref(out))
+    return rc, out.value
+
+
+def test_build_rejects_bad_patterns_before_any_cuda_call(lib):
+    # empty pattern, overlong pattern, null output: RK_EINVAL, *out cleared
+    assert _build_raw(lib, [b"ab", b""], [2, 0]) == (rk.RK_EINVAL, None)
+    long = b"x" * (rk.RK_MAX_PATTERN_LEN + 1)
+    assert _build_raw(lib, [long], [len(long)]) == (rk.RK_EINVAL, None)
+    assert lib.rk_build(None, None, 3, None, None) == rk.RK_EINVAL
+    for bad in (rk.BuildOpts(base_log2=61), rk.BuildOpts(filter=9), rk.BuildOpts(tile_bytes=1000),
+                rk.BuildOpts(stages=1), rk.BuildOpts(warps=40)):
+        assert _build_raw(lib, [b"ab"], [2], bad)[0] == rk.RK_EINVAL
+
+
+def test_entry_points_reject_null_table(lib):
+    assert lib.rk_scan_device(None, None, 0, None, 0, None, None) == rk.RK_EINVAL
+    assert lib.rk_sort_device(None, 0, None, 0, None, None, 0, None) == rk.RK_EINVAL
+    assert lib.rk_search_device(None, None, 0, None, 0, None, None, 0, None) == rk.RK_EINVAL
+    cnt = ctypes.c_uint64(7)
+    assert lib.rk_search(None, None, 0, None, 0, ctypes.byref(cnt)) == rk.RK_EINVAL
+    assert lib.rk_table_info_get(None, None) == rk.RK_EINVAL
+    assert lib.rk_workspace_bytes(None, 10) == 0
+    lib.rk_destroy(None)
+
+
+def test_window_hashes_rejects_bad_arguments(lib):
+    assert lib.rk_window_hashes_device(None, 10, 0, 8, None, None) == rk.RK_EINVAL
+    assert lib.rk_window_hashes_device(None, 10, 3, 61, None, None) == rk.RK_EINVAL
+    # L > n writes nothing and succeeds without touching the device
+    assert lib.rk_window_hashes_device(None, 2, 3, 8, None, None) == rk.RK_OK
+
+
+def test_unpack_keys():
+    keys = np.array([(5 << 40) | 17, (0 << 40) | ((1 << 40) - 1)], dtype=np.uint64)
+    ids, offs = rk.unpack_keys(keys)
+    assert ids.tolist() == [5, 0] and offs.tolist() == [17, (1 << 40) - 1]
