@@ -22,7 +22,7 @@ int scan_args_ok(const rk_table *t, const uint8_t *d_text, uint64_t n, const uin
 // ---- A2 on its own: Rabin hash of every window by a tiled rolling update --
 constexpr uint32_t kRollRun = 64;  // windows per thread
 
-__global__ void window_hash_kernel(const uint8_t *text, uint64_t n, uint32_t L, uint32_t k,
+__global__ void rk_window_hash_kernel(const uint8_t *text, uint64_t n, uint32_t L, uint32_t k,
                                    uint64_t *out) {
     const uint64_t nw = n - L + 1;
     const uint32_t s_out = (uint32_t)((uint64_t)k * (L - 1) % 61);  // B^(L-1) = 2^s_out
@@ -192,7 +192,7 @@ extern "C" int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32
         return RK_ECUDA;
     uint64_t runs = (n - L + 1 + kRollRun - 1) / kRollRun;
     uint64_t blocks = std::min<uint64_t>((runs + 255) / 256, (uint64_t)sms * 8);
-    window_hash_kernel<<<(uint32_t)std::max<uint64_t>(blocks, 1), 256, 0,
+    rk_window_hash_kernel<<<(uint32_t)std::max<uint64_t>(blocks, 1), 256, 0,
                          reinterpret_cast<cudaStream_t>(stream)>>>(d_text, n, L, base_log2,
                                                                      d_hashes);
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;

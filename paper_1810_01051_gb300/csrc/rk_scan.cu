@@ -212,7 +212,7 @@ __device__ __forceinline__ uint32_t stage1(const uint8_t *buf, uint32_t c, const
 }
 
 template <int MODE, bool Q4>
-__global__ void __launch_bounds__(1024, 1) scan_kernel(const __grid_constant__ ScanParams P) {
+__global__ void __launch_bounds__(1024, 1) rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ volatile uint32_t s_abort;
     const SmemLayout lay = smem_layout(P.tab.filter_bytes, P.warps, P.stages, P.tile, P.halo);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(1024, 1) scan_kernel(const __grid_constant__ S
 template <int MODE, bool Q4>
 cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                        cudaStream_t st) {
-    auto fn = scan_kernel<MODE, Q4>;
+    auto fn = rk_scan_tiles_kernel<MODE, Q4>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, threads, smem, st>>>(p);

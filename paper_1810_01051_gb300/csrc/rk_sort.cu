@@ -26,7 +26,7 @@ __device__ __forceinline__ bool sort_count(const unsigned long long *info, uint6
     return true;
 }
 
-__global__ void __launch_bounds__(kSortThreads) hist_kernel(const uint64_t *keys,
+__global__ void __launch_bounds__(kSortThreads) rk_sort_hist_kernel(const uint64_t *keys,
                                                             const unsigned long long *info,
                                                             uint64_t cap, uint32_t shift,
                                                             uint32_t *hist) {
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kSortThreads) hist_kernel(const uint64_t *keys
 }
 
 // Exclusive prefix sum, in place, of hist[0 .. 256*T) (digit-major order).
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(const unsigned long long *info,
+__global__ void __launch_bounds__(kScanThreads) rk_sort_prefix_kernel(const unsigned long long *info,
                                                             uint64_t cap, uint32_t *hist) {
     uint64_t M;
     uint32_t T;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const unsigned long 
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) scatter_kernel(const uint64_t *in, uint64_t *out,
+__global__ void __launch_bounds__(kSortThreads) rk_sort_scatter_kernel(const uint64_t *in, uint64_t *out,
                                                                const unsigned long long *info,
                                                                uint64_t cap, uint32_t shift,
                                                                const uint32_t *hist) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads) scatter_kernel(const uint64_t *i
     }
 }
 
-__global__ void copy_kernel(const uint64_t *in, uint64_t *out, const unsigned long long *info,
+__global__ void rk_sort_copy_kernel(const uint64_t *in, uint64_t *out, const unsigned long long *info,
                             uint64_t cap) {
     uint64_t M;
     uint32_t T;
@@ -186,13 +186,13 @@ int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capaci
     uint32_t grid = (uint32_t)std::max<uint64_t>(1, grid64);
     uint64_t *src = d_keys, *dst = tmp;
     for (uint32_t sh : shifts) {
-        hist_kernel<<<grid, kSortThreads, 0, stream>>>(src, info, capacity, sh, hist);
-        scan_kernel<<<1, kScanThreads, 0, stream>>>(info, capacity, hist);
-        scatter_kernel<<<grid, kSortThreads, 0, stream>>>(src, dst, info, capacity, sh, hist);
+        rk_sort_hist_kernel<<<grid, kSortThreads, 0, stream>>>(src, info, capacity, sh, hist);
+        rk_sort_prefix_kernel<<<1, kScanThreads, 0, stream>>>(info, capacity, hist);
+        rk_sort_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(src, dst, info, capacity, sh, hist);
         std::swap(src, dst);
     }
     if (src != d_keys)
-        copy_kernel<<<(uint32_t)t->sm_count * 4, 256, 0, stream>>>(src, d_keys, info, capacity);
+        rk_sort_copy_kernel<<<(uint32_t)t->sm_count * 4, 256, 0, stream>>>(src, d_keys, info, capacity);
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
