@@ -165,6 +165,30 @@ int rk_search(const rk_table *t, const uint8_t *h_text, uint64_t n, uint64_t *h_
 int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint32_t base_log2,
                             uint64_t *d_hashes, void *stream);
 
+/* ---- search without allocation ------------------------------------------
+ * No counterpart in the paper: a convenience for callers that cannot allocate.
+ *
+ * Some callers cannot call cudaMalloc or pass a workspace: applications whose
+ * own allocator has reserved all device memory (a foreign cudaMalloc fails),
+ * or latency-bound loops that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the device.  rk_search_device_noalloc does what
+ * rk_search_device does, but the sort's scratch space is a fixed array inside
+ * the library (RK_NOALLOC_MAX_KEYS keys: about 8.3 MB), reserved on every GPU
+ * where the library's device code is loaded and held until the process exits.
+ * It allocates nothing.
+ *   - capacity > RK_NOALLOC_MAX_KEYS is rejected with RK_EINVAL;
+ *   - the first call on each device looks up the array's device address
+ *     (once per device, with that device current): make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the one array, and it keeps the last
+ *     call's contents: calls that overlap on the GPU (other streams, other
+ *     threads, other tables) race on it and must be serialised by the caller.
+ * Other arguments, results and errors as rk_search_device.                  */
+#define RK_NOALLOC_MAX_KEYS (1u << 20)
+int rk_search_device_noalloc(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                             uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,12 +23,13 @@ RK_MAX_PATTERNS = (1 << 24) - 1
 RK_MAX_TEXT_LEN = (1 << 40) - 1
 RK_KEY_OFFSET_BITS = 40
 RK_FILTER_AUTO, RK_FILTER_REPLICATED, RK_FILTER_FLAT, RK_FILTER_NONE = range(4)
+RK_NOALLOC_MAX_KEYS = 1 << 20
 
 #: names of every function include/rk.h declares
 EXPORTS = [
     "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
-    "rk_window_hashes_device",
+    "rk_window_hashes_device", "rk_search_device_noalloc",
 ]
 
 
@@ -89,6 +90,8 @@ def load() -> ctypes.CDLL:
     L.rk_search.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64)]
     L.rk_window_hashes_device.restype = ctypes.c_int
     L.rk_window_hashes_device.argtypes = [vp, u64, u32, u32, vp, vp]
+    L.rk_search_device_noalloc.restype = ctypes.c_int
+    L.rk_search_device_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
     _lib = L
     return L
 
@@ -188,6 +191,16 @@ def rk_window_hashes_device(d_text, n: int, L: int, base_log2: int, d_hashes,
                             stream=None) -> None:
     _check(load().rk_window_hashes_device(_ptr(d_text), n, L, base_log2, _ptr(d_hashes),
                                           _stream(stream)), "rk_window_hashes_device")
+
+
+def rk_search_device_noalloc(table: int, d_text, n: int, d_keys, capacity: int, d_info,
+                             stream=None) -> None:
+    """rk_search_device for callers that cannot allocate: the sort's scratch is
+    a fixed array inside the library (capacity <= RK_NOALLOC_MAX_KEYS); calls
+    that overlap on the GPU race on it."""
+    _check(load().rk_search_device_noalloc(table, _ptr(d_text), n, _ptr(d_keys), capacity,
+                                           _ptr(d_info), _stream(stream)),
+           "rk_search_device_noalloc")
 
 
 # ------------------------------------------------------------------ key packing
