@@ -336,7 +336,8 @@ def run_ours(args, rank, world, local_rank):
         "hbm_frac_whole_step": (n + 8 * m) / (step_ms / 1e3) / 1e9 / peak,
         "build_ms": build_ms,
         "table": {kk: info_t[kk] for kk in ("filter", "filter_log2_bits", "warps", "tile_bytes",
-                                             "stages", "ctas_per_sm", "smem_bytes", "sm_count")},
+                                             "stages", "ctas_per_sm", "smem_bytes", "s2_smem_bytes",
+                                             "sm_count")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "scan_kernel", "peak_source": f"{peak_src} hbm_gbs",

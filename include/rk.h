@@ -93,6 +93,7 @@ typedef struct rk_table_info {
     uint32_t warps, tile_bytes, stages, ctas_per_sm, halo_bytes, smem_bytes;
     uint32_t sm_count;
     uint32_t device;
+    uint32_t s2_smem_bytes;    /* survivor-stage tables staged in shared memory (0: read from L2) */
     uint64_t device_bytes;     /* device memory held by the table */
 } rk_table_info;
 

@@ -29,14 +29,21 @@ struct GroupSlot {
     uint32_t count;  // 0 = empty slot
 };
 
-// One slot of the prefix map: a q-byte pattern prefix (big-endian value) and
-// the run [first, first+count) of distinct pattern lengths in gram_lens.
+// One slot of the prefix map: a q-byte pattern prefix (little-endian value),
+// the run [first, first+count) of distinct pattern lengths in gram_lens, and
+// `ext`, a 32-bit fingerprint set of the next four bytes (bytes q..q+3) of
+// the patterns with this prefix that are at least q + 4 bytes long.
 struct GramSlot {
     uint32_t key;
     uint32_t first;
     uint32_t count;  // 0 = empty slot
-    uint32_t pad;
+    uint32_t ext;
 };
+
+// Bit of `ext` for four bytes read as a little-endian word.
+__host__ __device__ __forceinline__ uint32_t ext_bit(uint32_t w) {
+    return (w * 0x9E3779B1u) >> 27;
+}
 
 // Device view of a table (pointers into one device allocation), passed to the
 // scan kernel by value.
@@ -45,7 +52,7 @@ struct DevTable {
     uint32_t filter_bytes;    // bytes of that image
     uint32_t filter_mode;     // FilterMode
     uint32_t filter_mask;     // address mask (see scan kernel)
-    uint32_t q;               // stage-1 key length in bytes, 1..4
+    uint32_t q;               // stage-1 key length in bytes, 1..4 (little-endian prefix)
 
     const GramSlot *grams;    // prefix map, 2^gram_bits slots
     uint32_t gram_bits;
@@ -64,6 +71,12 @@ struct DevTable {
     uint32_t n_patterns;
     uint32_t lmin, lmax;
     uint32_t base_log2;
+
+    // Every array above except the bit set lies in [s2_base, s2_base +
+    // s2_bytes): the survivor-stage tables, which the scan kernel may copy to
+    // shared memory as one block.
+    const uint8_t *s2_base;
+    uint32_t s2_bytes;
 };
 
 struct Tuning {
@@ -72,6 +85,7 @@ struct Tuning {
     uint32_t stages;
     uint32_t ctas_per_sm;
     uint32_t halo;         // bytes staged after each tile (multiple of 16, >= 16)
+    uint32_t s2_smem;      // survivor-stage table bytes copied to shared memory (0: global)
     uint32_t smem_bytes;   // dynamic shared memory per CTA
 };
 

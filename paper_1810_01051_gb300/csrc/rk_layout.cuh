@@ -6,12 +6,13 @@
 
 namespace rk {
 
-constexpr uint32_t kQueueCap = 64;    // stage-1 survivor entries per warp
-constexpr uint32_t kMatchCap = 128;   // buffered match keys per warp
-constexpr uint32_t kStagePad = 16;    // readable slack after each staged tile
+constexpr uint32_t kMaxTileBytes = 1u << 16;  // survivor positions are 16-bit
+constexpr uint32_t kQueueCap = 288;           // queued survivor windows per warp (u16 positions)
+constexpr uint32_t kMatchCap = 128;           // buffered match keys per warp
+constexpr uint32_t kStagePad = 16;            // readable slack after each staged tile
 
 struct SmemLayout {
-    uint32_t filter_off, bar_off, queue_off, qcount_off, mcount_off, match_off, stage_off;
+    uint32_t filter_off, s2_off, bar_off, queue_off, mcount_off, match_off, stage_off;
     uint32_t stage_stride;
     uint32_t total;
 };
@@ -20,19 +21,21 @@ __host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) {
     return (x + a - 1) / a * a;
 }
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t filter_bytes, uint32_t warps,
-                                                  uint32_t stages, uint32_t tile_bytes,
-                                                  uint32_t halo) {
+// s2_bytes: bytes of the survivor-stage tables copied into shared memory (0 =
+// they stay in global memory).
+__host__ __device__ inline SmemLayout smem_layout(uint32_t filter_bytes, uint32_t s2_bytes,
+                                                  uint32_t warps, uint32_t stages,
+                                                  uint32_t tile_bytes, uint32_t halo) {
     SmemLayout L{};
     uint32_t off = 0;
     L.filter_off = off;
     off = align_up(off + filter_bytes, 128);
+    L.s2_off = off;
+    off = align_up(off + s2_bytes, 128);
     L.bar_off = off;
     off = align_up(off + 2 * stages * 8, 16);
     L.queue_off = off;
-    off = align_up(off + warps * kQueueCap * 4, 16);
-    L.qcount_off = off;
-    off = align_up(off + warps * 4, 16);
+    off = align_up(off + warps * kQueueCap * 2, 16);
     L.mcount_off = off;
     off = align_up(off + warps * 4, 16);
     L.match_off = off;

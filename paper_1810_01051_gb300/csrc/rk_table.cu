@@ -3,10 +3,10 @@
 // Section 3.1 computes the pattern hash once on the host and passes it to the
 // kernel.  For a pattern set the host builds, in one device allocation:
 //   - stage-1 bit set over the q-byte prefixes of all patterns (q = min(4,
-//     shortest length)), keyed by the prefix's big-endian value (its Rabin
-//     hash for B = 256, exact because 256^q < 2^61 - 1);
+//     shortest length)), keyed by the prefix read as a little-endian word;
 //   - prefix map: exact q-byte prefix -> distinct lengths of the patterns
-//     that start with it;
+//     that start with it, plus a 32-bit fingerprint set of their next four
+//     bytes;
 //   - one open-addressing table per pattern length L, keyed by the Rabin
 //     hash h_B(P) = sum_i P[i] * B^(L-1-i) mod (2^61 - 1), B = 2^base_log2,
 //     each slot naming the ids of the patterns of that length and hash;
@@ -42,9 +42,10 @@ uint32_t ceil_log2(uint64_t x) {
     return b;
 }
 
+// The first q bytes as a little-endian integer.
 uint32_t prefix_key(const uint8_t *s, uint32_t q) {
     uint32_t v = 0;
-    for (uint32_t i = 0; i < q; ++i) v = (v << 8) | s[i];
+    for (uint32_t i = 0; i < q; ++i) v |= (uint32_t)s[i] << (8 * i);
     return v;
 }
 
@@ -96,8 +97,8 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     uint32_t tile = o.tile_bytes ? o.tile_bytes : 32768;
     uint32_t stages = o.stages ? o.stages : 3;
     uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
-    // tile + halo is one bulk copy; an mbarrier phase counts < 2^20 transaction bytes
-    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > (1u << 19) ||
+    // survivor positions within a tile are 16-bit
+    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > kMaxTileBytes ||
         stages < 2 || stages > 8 || cps < 1 || cps > 8)
         return RK_EINVAL;
 
@@ -126,9 +127,15 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
 
     // ---- prefix map: q-byte prefix -> distinct lengths ----------------------
     std::unordered_map<uint32_t, std::vector<uint32_t>> gram_to_lens;
+    std::unordered_map<uint32_t, uint32_t> gram_ext;
     gram_to_lens.reserve(k * 2 + 1);
-    for (uint32_t i = 0; i < k; ++i)
-        gram_to_lens[prefix_key(patterns + src_off[i], q)].push_back(plen[i]);
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint8_t *p = patterns + src_off[i];
+        uint32_t key = prefix_key(p, q);
+        gram_to_lens[key].push_back(plen[i]);
+        uint32_t &ext = gram_ext[key];
+        if (plen[i] >= q + 4) ext |= 1u << ext_bit(prefix_key(p + q, 4));
+    }
     std::vector<uint32_t> gram_keys;
     gram_keys.reserve(gram_to_lens.size());
     for (auto &kv : gram_to_lens) {
@@ -147,7 +154,7 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
         uint32_t idx = (key * kGramMult) >> (32 - gram_bits);
         uint32_t mask = (1u << gram_bits) - 1;
         while (grams[idx].count) idx = (idx + 1) & mask;
-        grams[idx] = GramSlot{key, (uint32_t)gram_lens.size(), (uint32_t)v.size(), 0};
+        grams[idx] = GramSlot{key, (uint32_t)gram_lens.size(), (uint32_t)v.size(), gram_ext[key]};
         gram_lens.insert(gram_lens.end(), v.begin(), v.end());
     }
 
@@ -235,6 +242,7 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     size_t o_poff = b.add(k * 8 + 8);
     size_t o_plen = b.add(k * 4 + 4);
     size_t o_lens = b.add(lengths.size() * 4 + 4);
+    b.add(0);  // the blob ends on a 256-byte boundary: whole 16-byte copies stay inside
     uint8_t *hb = b.bytes.data();
     if (!fimg.empty()) memcpy(hb + o_filter, fimg.data(), fimg.size() * 4);
     memcpy(hb + o_grams, grams.data(), grams.size() * sizeof(GramSlot));
@@ -247,6 +255,7 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     if (k) memcpy(hb + o_plen, plen.data(), k * 4);
     if (!lengths.empty()) memcpy(hb + o_lens, lengths.data(), lengths.size() * 4);
 
+    if (b.bytes.size() - o_grams > 0xFFFFFFFFull) return RK_EINVAL;  // tables above 4 GiB
     int dev = 0, sms = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RK_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -259,13 +268,26 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     uint32_t halo = align_up(std::max<uint32_t>(lmax - 1, 1), 16);
     uint32_t fbytes = (uint32_t)(fimg.size() * 4);
     uint32_t limit = (uint32_t)smem_optin / cps - 1024;  // room for static shared memory
-    SmemLayout lay = smem_layout(fbytes, warps, stages, tile, halo);
+    // The survivor-stage tables go to shared memory when they fit beside the
+    // requested pipeline (or beside a two-stage one); otherwise they are read
+    // from global memory (L2).
+    const uint64_t s2_total = b.bytes.size() - o_grams;
+    uint32_t s2 = 0;
+    if (s2_total <= limit) {
+        if (smem_layout(fbytes, (uint32_t)s2_total, warps, stages, tile, halo).total <= limit) {
+            s2 = (uint32_t)s2_total;
+        } else if (smem_layout(fbytes, (uint32_t)s2_total, warps, 2, tile, halo).total <= limit) {
+            s2 = (uint32_t)s2_total;
+            stages = 2;
+        }
+    }
+    SmemLayout lay = smem_layout(fbytes, s2, warps, stages, tile, halo);
     while (lay.total > limit) {
         if (stages > 2) --stages;
         else if (tile > 4 * halo && tile > 4096) tile /= 2;
         else return RK_EINVAL;
         tile = tile / 16 * 16;
-        lay = smem_layout(fbytes, warps, stages, tile, halo);
+        lay = smem_layout(fbytes, s2, warps, stages, tile, halo);
     }
 
     rk_table *t = new (std::nothrow) rk_table();
@@ -305,7 +327,9 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     d.lmin = lmin;
     d.lmax = lmax;
     d.base_log2 = base_log2;
-    t->tune = Tuning{warps, tile, stages, cps, halo, lay.total};
+    d.s2_base = dm + o_grams;
+    d.s2_bytes = (uint32_t)s2_total;
+    t->tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
     t->n_grams = D;
     t->filter_log2_bits = mode == kFilterNone ? 0 : fbits;
     t->filter_opt = o.filter;
@@ -355,6 +379,7 @@ extern "C" int rk_table_info_get(const rk_table *t, rk_table_info *info) {
     r.smem_bytes = t->tune.smem_bytes;
     r.sm_count = (uint32_t)t->sm_count;
     r.device = (uint32_t)t->device;
+    r.s2_smem_bytes = t->tune.s2_smem;
     r.device_bytes = t->d_bytes;
     *info = r;
     return RK_OK;

@@ -48,7 +48,7 @@ class TableInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_patterns", "min_len", "max_len", "n_lengths", "gram_len", "base_log2", "filter",
         "filter_log2_bits", "filter_smem_bytes", "n_grams", "warps", "tile_bytes", "stages",
-        "ctas_per_sm", "halo_bytes", "smem_bytes", "sm_count", "device")] + [
+        "ctas_per_sm", "halo_bytes", "smem_bytes", "sm_count", "device", "s2_smem_bytes")] + [
         ("device_bytes", ctypes.c_uint64)]
 
 
