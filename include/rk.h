@@ -78,8 +78,9 @@ typedef struct rk_build_opts {
     uint32_t filter;           /* RK_FILTER_* */
     uint32_t filter_log2_bits; /* prefilter size in bits, log2 (default: by pattern count) */
     uint32_t warps;            /* consumer warps per CTA, 1..32 (default 16) */
-    uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16 (default 32768) */
-    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 3) */
+    uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16, <= 65536
+                                  (default 49152) */
+    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */
     uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
 } rk_build_opts;
 
@@ -174,7 +175,7 @@ int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint3
  * or latency-bound loops that cannot afford cudaMalloc/cudaFree, which may
  * synchronise the device.  rk_search_device_noalloc does what
  * rk_search_device does, but the sort's scratch space is a fixed array inside
- * the library (RK_NOALLOC_MAX_KEYS keys: about 8.3 MB), reserved on every GPU
+ * the library (RK_NOALLOC_MAX_KEYS keys: about 12 MB), reserved on every GPU
  * where the library's device code is loaded and held until the process exits.
  * It allocates nothing.
  *   - capacity > RK_NOALLOC_MAX_KEYS is rejected with RK_EINVAL;

@@ -13,14 +13,14 @@
 #include <mutex>
 
 #include "rk_internal.cuh"
+#include "rk_sortws.cuh"
 
 namespace {
 
 // Scratch for an output of up to RK_NOALLOC_MAX_KEYS keys: the sort's
-// ping-pong buffer (8 bytes per key) plus one 256-bin histogram per 4096 keys,
-// each part 256-byte aligned, plus 256 bytes of slack.
-constexpr uint64_t kNoAllocKeys = RK_NOALLOC_MAX_KEYS;
-constexpr uint64_t kNoAllocBytes = kNoAllocKeys * 8 + 256ull * ((kNoAllocKeys + 4095) / 4096) * 4 + 256;
+// workspace for that capacity (ping-pong key buffer, digit totals and
+// look-back words).
+constexpr uint64_t kNoAllocBytes = rk::sort_ws_bytes(RK_NOALLOC_MAX_KEYS);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -60,8 +60,9 @@ extern "C" int rk_search_device_noalloc(const rk_table *t, const uint8_t *d_text
     if ((rc = scratch_address(t->device, &scratch))) return rc;
     rc = rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
     if (rc) return rc;
-    // The sort writes every histogram entry and every buffered key it later
-    // reads, so leftovers from an earlier call need no clearing.
+    // The sort clears its counters, digit totals and look-back words itself
+    // before using them, and writes every buffered key before reading it, so
+    // leftovers from an earlier call do no harm.
     return rk::launch_sort(t, n, d_keys, capacity, d_info, scratch, kNoAllocBytes,
                            reinterpret_cast<cudaStream_t>(stream));
 }

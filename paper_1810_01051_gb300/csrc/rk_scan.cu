@@ -247,8 +247,10 @@ __device__ __forceinline__ Chunk load_chunk(const uint8_t *buf, uint32_t c, uint
 }
 
 // MAXW: most consumer warps this instance is launched with; the register
-// budget per thread follows from (MAXW + 1) warps per SM.
-template <int MODE, bool Q4, int MAXW>
+// budget per thread follows from (MAXW + 1) warps per SM.  S2S: the
+// survivor-stage tables are staged in shared memory (their loads then
+// compile to shared-memory loads).
+template <int MODE, bool Q4, int MAXW, bool S2S>
 __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         uint4 *dst = reinterpret_cast<uint4 *>(sfilt);
         for (uint32_t i = tid; i < P.tab.filter_bytes / 16u; i += blockDim.x) dst[i] = src[i];
     }
-    if (P.s2_smem) {
+    if (S2S) {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.tab.s2_base);
         uint4 *dst = reinterpret_cast<uint4 *>(ss2);
         for (uint32_t i = tid; i < (P.s2_smem + 15u) / 16u; i += blockDim.x) dst[i] = src[i];
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     {
         const DevTable &T = P.tab;
         const uint8_t *from = T.s2_base;
-        const uint8_t *to = P.s2_smem ? ss2 : T.s2_base;
+        const uint8_t *to = S2S ? ss2 : T.s2_base;
         s2.grams = rebase(T.grams, from, to);
         s2.gram_lens = rebase(T.gram_lens, from, to);
         s2.group_hdr = rebase(T.group_hdr, from, to);
@@ -417,7 +419,8 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
 template <int MODE, bool Q4, int MAXW>
 cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                      cudaStream_t st) {
-    auto fn = rk_scan_tiles_kernel<MODE, Q4, MAXW>;
+    auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true>
+                        : rk_scan_tiles_kernel<MODE, Q4, MAXW, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, threads, smem, st>>>(p);

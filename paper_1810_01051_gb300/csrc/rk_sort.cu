@@ -3,146 +3,182 @@
 //
 // Least-significant-digit radix sort over 8-bit digits.  Only the digits
 // that can be non-zero are sorted: those of the offset field (bits below
-// ceil(log2(n))) and of the id field (bits 40.. up to ceil(log2(k))).  Each
-// pass is histogram -> exclusive scan -> stable scatter, every kernel reading
-// the key count from d_info on the device, so nothing returns to the host
-// between the scan and the sorted list.
+// ceil(log2(n))) and of the id field (bits 40.. up to ceil(log2(k))).
+//
+//   1. one histogram kernel reads the keys once and counts every pass's
+//      digits (the totals do not depend on the order), and clears the
+//      per-tile status words of the passes;
+//   2. one kernel per pass: each CTA takes the next tile of 4096 keys from a
+//      counter, ranks its keys stably (warp match + per-warp digit counters),
+//      publishes its digit counts, adds up the counts of the tiles before it
+//      by looking back through their published words (decoupled look-back),
+//      and scatters.  Look-back waits are bounded: a wait that runs out
+//      records RK_ETIMEOUT in d_info[1].
+//
+// Every kernel reads the key count from d_info on the device, so nothing
+// returns to the host between the scan and the sorted list.
 #include "rk_internal.cuh"
+#include "rk_sortws.cuh"
 
 namespace rk {
 namespace {
 
-constexpr uint32_t kSortThreads = 256;
-constexpr uint32_t kSortRounds = 16;
-constexpr uint32_t kSortTile = kSortThreads * kSortRounds;  // keys per tile
-constexpr uint32_t kScanThreads = 1024;
+constexpr uint32_t kThreads = 256;
+constexpr uint32_t kWarps = kThreads / 32;
+constexpr uint32_t kPerWarp = kSortTile / kWarps;  // 512 consecutive keys per warp
+constexpr uint64_t kFlagAgg = 1ull << 62;          // tile's own counts published
+constexpr uint64_t kFlagInc = 2ull << 62;          // inclusive prefix published
+constexpr uint64_t kCountMask = (1ull << 62) - 1;
+constexpr uint64_t kLookbackTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ bool sort_count(const unsigned long long *info, uint64_t cap,
                                            uint64_t *m, uint32_t *tiles) {
-    uint64_t M = info[0];
-    if (M > cap || M < 2) return false;
+    const uint64_t M = info[0];
+    if (M > cap || M < 2 || info[1] != RK_OK) return false;
     *m = M;
     *tiles = (uint32_t)((M + kSortTile - 1) / kSortTile);
     return true;
 }
 
-__global__ void __launch_bounds__(kSortThreads) rk_sort_hist_kernel(const uint64_t *keys,
-                                                            const unsigned long long *info,
-                                                            uint64_t cap, uint32_t shift,
-                                                            uint32_t *hist) {
-    uint64_t M;
-    uint32_t T;
-    if (!sort_count(info, cap, &M, &T)) return;
-    __shared__ uint32_t h[256];
-    const uint32_t tid = threadIdx.x;
-    for (uint32_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
-        h[tid] = 0;
-        __syncthreads();
-        const uint64_t base = (uint64_t)tile * kSortTile;
-#pragma unroll 4
-        for (uint32_t r = 0; r < kSortRounds; ++r) {
-            uint64_t idx = base + r * kSortThreads + tid;
-            if (idx < M) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        hist[(uint64_t)tid * T + tile] = h[tid];
-        __syncthreads();
-    }
-}
+struct Shifts {
+    uint32_t s[kMaxSortPasses];
+    uint32_t n;
+};
 
-// Exclusive prefix sum, in place, of hist[0 .. 256*T) (digit-major order).
-__global__ void __launch_bounds__(kScanThreads) rk_sort_prefix_kernel(const unsigned long long *info,
-                                                            uint64_t cap, uint32_t *hist) {
+__global__ void __launch_bounds__(kThreads) rk_sort_hist_kernel(const uint64_t *keys,
+                                                                const unsigned long long *info,
+                                                                uint64_t cap, Shifts sh,
+                                                                uint32_t *ghist,
+                                                                uint64_t *status,
+                                                                uint64_t tiles_max) {
     uint64_t M;
     uint32_t T;
     if (!sort_count(info, cap, &M, &T)) return;
-    __shared__ uint32_t wsum[kScanThreads / 32];
-    __shared__ uint32_t s_carry;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t total = 256ull * T;
-    if (tid == 0) s_carry = 0;
+    __shared__ uint32_t h[kMaxSortPasses][256];
+    for (uint32_t p = 0; p < sh.n; ++p) h[p][threadIdx.x] = 0;
     __syncthreads();
-    for (uint64_t base = 0; base < total; base += kScanThreads * 4ull) {
-        uint32_t v[4], s = 0;
-        for (int j = 0; j < 4; ++j) {
-            uint64_t idx = base + tid * 4ull + j;
-            v[j] = idx < total ? hist[idx] : 0;
-            s += v[j];
-        }
-        uint32_t incl = s;
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= (uint32_t)d) incl += o;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t ws = wsum[lane], wi = ws;
-            for (int d = 1; d < 32; d <<= 1) {
-                uint32_t o = __shfl_up_sync(0xffffffffu, wi, d);
-                if (lane >= (uint32_t)d) wi += o;
-            }
-            wsum[lane] = wi - ws;  // exclusive warp offsets
-        }
-        __syncthreads();
-        uint32_t run = s_carry + wsum[warp] + incl - s;
-        for (int j = 0; j < 4; ++j) {
-            uint64_t idx = base + tid * 4ull + j;
-            if (idx < total) hist[idx] = run;
-            run += v[j];
-        }
-        __syncthreads();
-        if (tid == kScanThreads - 1) s_carry = run;
-        __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += stride) {
+        const uint64_t k = keys[i];
+        for (uint32_t p = 0; p < sh.n; ++p) atomicAdd(&h[p][(uint32_t)(k >> sh.s[p]) & 255u], 1u);
     }
+    // clear the look-back words of every pass (tiles actually used)
+    const uint64_t per_pass = (uint64_t)T * 256u;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < sh.n * per_pass;
+         i += stride)
+        status[(i / per_pass) * tiles_max * 256u + i % per_pass] = 0;
+    __syncthreads();
+    for (uint32_t p = 0; p < sh.n; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
-__global__ void __launch_bounds__(kSortThreads) rk_sort_scatter_kernel(const uint64_t *in, uint64_t *out,
-                                                               const unsigned long long *info,
-                                                               uint64_t cap, uint32_t shift,
-                                                               const uint32_t *hist) {
+__global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
+    const uint64_t *in, uint64_t *out, unsigned long long *info, uint64_t cap, uint32_t shift,
+    const uint32_t *ghist, uint64_t *status, uint32_t *counter) {
     uint64_t M;
     uint32_t T;
     if (!sort_count(info, cap, &M, &T)) return;
-    constexpr uint32_t NW = kSortThreads / 32;
-    __shared__ uint32_t cnt[NW][256];
-    __shared__ uint32_t off[NW][256];
-    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t wcnt[kWarps][256];  // per-warp digit counts, then exclusive offsets
+    __shared__ uint32_t dbase[256];         // global start of each digit in this tile
+    __shared__ uint32_t s_tile;
+    __shared__ int s_abort;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t w = 0; w < NW; ++w) cnt[w][tid] = 0;
-    for (uint32_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+
+    // exclusive prefix of this pass's digit totals (thread d owns digit d)
+    uint32_t gbase;
+    {
+        __shared__ uint32_t tot[256];
+        tot[tid] = ghist[tid];
         __syncthreads();
-        gbase[tid] = hist[(uint64_t)tid * T + tile];
-        uint32_t run = 0;  // keys of digit `tid` already placed in this tile
-        const uint64_t base = (uint64_t)tile * kSortTile;
-        for (uint32_t r = 0; r < kSortRounds; ++r) {
-            const uint64_t idx = base + r * kSortThreads + tid;
+        uint32_t acc = 0;
+        for (uint32_t d = 0; d < tid; ++d) acc += tot[d];
+        gbase = acc;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_tile = atomicAdd(counter, 1u);
+            s_abort = 0;
+        }
+        for (uint32_t w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= T) return;
+
+        // stable local ranks: warp w takes keys [w*512, (w+1)*512) of the tile
+        const uint64_t base = (uint64_t)tile * kSortTile + (uint64_t)warp * kPerWarp;
+        uint64_t key[kPerWarp / 32];
+        uint32_t rank[kPerWarp / 32];
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+            const uint64_t idx = base + r * 32 + lane;
             const bool valid = idx < M;
-            const uint64_t key = valid ? in[idx] : 0;
-            const uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+            key[r] = valid ? in[idx] : 0;
+            const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t rank = __popc(peers & lt);
-            if (valid && rank == 0) cnt[warp][d] = __popc(peers);
-            __syncthreads();
-            {  // thread `tid` owns digit `tid`: offsets of each warp's run
-                uint32_t acc = run;
-                for (uint32_t w = 0; w < NW; ++w) {
-                    uint32_t c = cnt[w][tid];
-                    cnt[w][tid] = 0;
-                    off[w][tid] = acc;
-                    acc += c;
+            const uint32_t before = valid ? wcnt[warp][d] : 0;
+            rank[r] = before + __popc(peers & lt);
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // thread d: per-warp exclusive offsets and the tile's count of digit d
+        uint32_t cnt = 0;
+        for (uint32_t w = 0; w < kWarps; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = cnt;
+            cnt += c;
+        }
+        // decoupled look-back over the tiles before this one
+        uint64_t *st = status + (uint64_t)tile * 256u + tid;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            *reinterpret_cast<volatile uint64_t *>(st) = kFlagInc | cnt;
+        } else {
+            *reinterpret_cast<volatile uint64_t *>(st) = kFlagAgg | cnt;
+            int64_t j = (int64_t)tile - 1;
+            uint64_t t0 = 0;
+            while (j >= 0) {
+                const uint64_t v = *reinterpret_cast<volatile const uint64_t *>(
+                    status + (uint64_t)j * 256u + tid);
+                if (v & kFlagInc) {
+                    excl += v & kCountMask;
+                    break;
                 }
-                run = acc;
+                if (v & kFlagAgg) {
+                    excl += v & kCountMask;
+                    --j;
+                    continue;
+                }
+                // predecessor not published yet (it was claimed earlier, so it runs)
+                if (t0 == 0) t0 = globaltimer_ns();
+                else if (globaltimer_ns() - t0 > kLookbackTimeoutNs) {
+                    info[1] = RK_ETIMEOUT;
+                    s_abort = 1;
+                    break;
+                }
             }
-            __syncthreads();
-            if (valid) out[gbase[d] + off[warp][d] + rank] = key;
+            __threadfence();
+            *reinterpret_cast<volatile uint64_t *>(st) = kFlagInc | (excl + cnt);
+        }
+        dbase[tid] = gbase + (uint32_t)excl;
+        __syncthreads();
+        if (s_abort) return;
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+            const uint64_t idx = base + r * 32 + lane;
+            if (idx < M) {
+                const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+                out[dbase[d] + wcnt[warp][d] + rank[r]] = key[r];
+            }
         }
     }
 }
 
-__global__ void rk_sort_copy_kernel(const uint64_t *in, uint64_t *out, const unsigned long long *info,
-                            uint64_t cap) {
+__global__ void rk_sort_copy_kernel(const uint64_t *in, uint64_t *out,
+                                    const unsigned long long *info, uint64_t cap) {
     uint64_t M;
     uint32_t T;
     if (!sort_count(info, cap, &M, &T)) return;
@@ -157,42 +193,46 @@ uint32_t bits_for(uint64_t max_value) {
     return b;
 }
 
-uint64_t max_sort_tiles(uint64_t capacity) { return (capacity + kSortTile - 1) / kSortTile; }
-
 }  // namespace
 
-uint64_t sort_workspace_bytes(uint64_t capacity) {
-    uint64_t keys = (capacity * 8 + 255) / 256 * 256;
-    uint64_t hist = (256ull * max_sort_tiles(capacity) * 4 + 255) / 256 * 256;
-    return keys + hist + 256;
-}
+uint64_t sort_workspace_bytes(uint64_t capacity) { return sort_ws_bytes(capacity); }
 
 int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream) {
     if (capacity < 2 || n == 0 || t->dev.n_patterns == 0) return RK_OK;
-    if (ws_bytes < sort_workspace_bytes(capacity)) return RK_EINVAL;
-    uint64_t *tmp = reinterpret_cast<uint64_t *>(d_ws);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(d_ws) +
-                                                  (capacity * 8 + 255) / 256 * 256);
-    const unsigned long long *info = reinterpret_cast<const unsigned long long *>(d_info);
+    if (ws_bytes < sort_ws_bytes(capacity)) return RK_EINVAL;
+    const SortWsLayout L = sort_ws_layout(capacity);
+    uint8_t *ws = reinterpret_cast<uint8_t *>(d_ws);
+    uint64_t *tmp = reinterpret_cast<uint64_t *>(ws + L.tmp_off);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(ws + L.ctrl_off);
+    uint32_t *ghist = reinterpret_cast<uint32_t *>(ws + L.ghist_off);
+    uint64_t *status = reinterpret_cast<uint64_t *>(ws + L.status_off);
+    unsigned long long *info =
+        reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(d_info));
 
-    std::vector<uint32_t> shifts;
+    Shifts sh{};
     const uint32_t ob = bits_for(n - 1), pb = bits_for(t->dev.n_patterns - 1);
-    for (uint32_t s = 0; s < ob; s += 8) shifts.push_back(s);
-    for (uint32_t s = 0; s < pb; s += 8) shifts.push_back(RK_KEY_OFFSET_BITS + s);
+    for (uint32_t s = 0; s < ob; s += 8) sh.s[sh.n++] = s;
+    for (uint32_t s = 0; s < pb; s += 8) sh.s[sh.n++] = RK_KEY_OFFSET_BITS + s;
+    if (sh.n == 0) return RK_OK;
 
-    uint64_t tiles = max_sort_tiles(capacity);
-    uint64_t grid64 = std::min<uint64_t>(tiles, (uint64_t)t->sm_count * 4);
-    uint32_t grid = (uint32_t)std::max<uint64_t>(1, grid64);
-    uint64_t *src = d_keys, *dst = tmp;
-    for (uint32_t sh : shifts) {
-        rk_sort_hist_kernel<<<grid, kSortThreads, 0, stream>>>(src, info, capacity, sh, hist);
-        rk_sort_prefix_kernel<<<1, kScanThreads, 0, stream>>>(info, capacity, hist);
-        rk_sort_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(src, dst, info, capacity, sh, hist);
-        std::swap(src, dst);
+    if (cudaMemsetAsync(ws + L.ctrl_off, 0, L.status_off - L.ctrl_off, stream) != cudaSuccess)
+        return RK_ECUDA;
+    const uint32_t grid = (uint32_t)t->sm_count * 4;
+    const uint64_t tiles = L.tiles;
+    rk_sort_hist_kernel<<<grid, kThreads, 0, stream>>>(d_keys, info, capacity, sh, ghist, status,
+                                                       tiles);
+    for (uint32_t p = 0; p < sh.n; ++p) {
+        const uint64_t *src = (p & 1) ? tmp : d_keys;
+        uint64_t *dst = (p & 1) ? d_keys : tmp;
+        const uint32_t pgrid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)t->sm_count * 8);
+        rk_sort_pass_kernel<<<pgrid, kThreads, 0, stream>>>(
+            src, dst, info, capacity, sh.s[p], ghist + p * 256, status + (uint64_t)p * tiles * 256,
+            counters + p);
     }
-    if (src != d_keys)
-        rk_sort_copy_kernel<<<(uint32_t)t->sm_count * 4, 256, 0, stream>>>(src, d_keys, info, capacity);
+    if (sh.n & 1)
+        rk_sort_copy_kernel<<<(uint32_t)t->sm_count * 4, 256, 0, stream>>>(tmp, d_keys, info,
+                                                                           capacity);
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 

@@ -94,8 +94,9 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
     if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
     uint32_t warps = o.warps ? o.warps : 16;
-    uint32_t tile = o.tile_bytes ? o.tile_bytes : 32768;
-    uint32_t stages = o.stages ? o.stages : 3;
+    // default: 48 KiB tiles (three 16 KiB rounds of 16 warps), two in flight
+    uint32_t tile = o.tile_bytes ? o.tile_bytes : 49152;
+    uint32_t stages = o.stages ? o.stages : 2;
     uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
     // survivor positions within a tile are 16-bit
     if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > kMaxTileBytes ||
