@@ -167,6 +167,88 @@ int rk_search(const rk_table *t, const uint8_t *h_text, uint64_t n, uint64_t *h_
 int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint32_t base_log2,
                             uint64_t *d_hashes, void *stream);
 
+/* ---- batched search --------------------------------------------------------
+ * Many texts, each searched with its own pattern table, in one launch: the
+ * persistent batched kernel with its sort captured in a CUDA graph.
+ *
+ * A match of a batch is one key
+ *     key = (item << (id_bits + offset_bits)) | (id << offset_bits) | x
+ * (field widths in rk_batch_info), so ascending keys list every item's matches
+ * together, in ascending (pattern id, offset) order; the item offsets give
+ * where each item's run starts.                                              */
+typedef struct rk_tableset rk_tableset;
+typedef struct rk_batch rk_batch;
+
+/* n_tables pattern tables in one device allocation.  patterns holds all
+ * tables' patterns concatenated (table 0 first), lens their lengths,
+ * patterns_per_table[i] the count of table i (ids restart at 0 per table; 0
+ * patterns allowed).  opts: NULL or base_log2, filter (RK_FILTER_AUTO or
+ * RK_FILTER_FLAT: a flat bit set; RK_FILTER_NONE: no prefilter) and
+ * filter_log2_bits; the launch fields are ignored.
+ * Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA.                                    */
+int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, const uint32_t *lens,
+                      const uint32_t *patterns_per_table, const rk_build_opts *opts,
+                      rk_tableset **out);
+void rk_tableset_destroy(rk_tableset *ts);
+
+typedef struct rk_batch_opts {
+    uint32_t max_items;        /* texts per batch, >= 1 */
+    uint64_t max_text_len;     /* longest text, >= 1 (sets offset_bits) */
+    uint64_t max_total_bytes;  /* most text bytes in one batch */
+    uint64_t capacity;         /* match keys per batch, < 2^32 */
+    uint32_t warps;            /* consumer warps per CTA (default 16) */
+    uint32_t tile_bytes;       /* bytes per tile, multiple of 16, <= 65536 (default 32768) */
+    uint32_t stages;           /* tiles in flight per CTA (default 2) */
+    uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
+    uint32_t s2_in_smem;       /* 1: the survivor tables travel with each tile into shared
+                                  memory; 0: they are read from L2 (default) */
+} rk_batch_opts;
+
+typedef struct rk_batch_info {
+    uint32_t offset_bits, id_bits, item_bits;  /* key fields */
+    uint32_t warps, tile_bytes, stages, ctas_per_sm, s2_in_smem, smem_bytes;
+    uint32_t n_chunks, max_chunks;             /* work chunks of the current batch */
+} rk_batch_info;
+
+/* A batch engine over a table set: device buffers for opts' limits and the
+ * captured graph.  The table set must outlive the batch.
+ * Errors: RK_EINVAL (limits, fields wider than 64 bits), RK_ENOMEM, RK_ECUDA. */
+int rk_batch_create(const rk_tableset *ts, const rk_batch_opts *opts, rk_batch **out);
+void rk_batch_destroy(rk_batch *b);
+int rk_batch_info_get(const rk_batch *b, rk_batch_info *info);
+
+/* Describe the next batch: item i searches d_texts[i][0 .. text_lens[i]) (device
+ * memory, any alignment, kept valid until the run completes) with table
+ * table_of_item[i].  Host arrays; the descriptors are copied on `stream` and
+ * the call returns once they are on the device.  Errors: RK_EINVAL, RK_ECUDA. */
+int rk_batch_set(rk_batch *b, uint32_t n_items, const uint32_t *table_of_item,
+                 const uint8_t *const *d_texts, const uint64_t *text_lens, void *stream);
+
+/* Run the batch: one graph launch (persistent scan of all items, sort,
+ * item offsets) on `stream`, asynchronous.  Errors: RK_EINVAL, RK_ECUDA.    */
+int rk_batch_run(rk_batch *b, void *stream);
+
+/* Device pointers owned by the batch (valid until rk_batch_destroy): the
+ * sorted keys, n_items + 1 item offsets into them (item i's matches are keys
+ * [offsets[i], offsets[i+1])), and the header {count, status}.  When count >
+ * capacity the keys and offsets are not valid.                              */
+int rk_batch_results(const rk_batch *b, const uint64_t **d_keys, const uint64_t **d_item_offsets,
+                     const uint64_t **d_info);
+
+/* Copy the results of the last run to host memory and wait: h_info[0..2)
+ * (count, status); if the run succeeded and fit, h_item_offsets[0 .. n_items]
+ * (may be NULL) and the first min(count, key_cap) keys (h_keys may be NULL).
+ * Errors: RK_EINVAL, RK_ECUDA.                                               */
+int rk_batch_read(const rk_batch *b, uint64_t *h_keys, uint64_t key_cap, uint64_t *h_item_offsets,
+                  uint64_t *h_info, void *stream);
+
+/* Autotuner: time up to max_candidates launch shapes (tile size, warps,
+ * stages, CTAs per SM, survivor-table placement; 0 = all that fit), each
+ * `reps` times on the current batch, keep the fastest and re-capture the
+ * graph.  *best_ms (may be NULL) gets the best scan time.  Synchronous.     */
+int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t reps, double *best_ms,
+                      void *stream);
+
 /* ---- search without allocation ------------------------------------------
  * No counterpart in the paper: a convenience for callers that cannot allocate.
  *

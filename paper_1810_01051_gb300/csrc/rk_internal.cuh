@@ -118,6 +118,20 @@ struct rk_table {
 
 namespace rk {
 
+// Host image of one pattern table (all parts 256-byte aligned) and the
+// offsets of its parts; `meta` holds the device view's non-pointer fields.
+struct TableBlob {
+    std::vector<uint8_t> bytes;
+    size_t o_filter = 0, o_grams = 0, o_glens = 0, o_ghdr = 0, o_slots = 0, o_gpids = 0,
+           o_pbytes = 0, o_poff = 0, o_plen = 0, o_lens = 0;
+    DevTable meta{};
+    uint32_t n_grams = 0, filter_log2_bits = 0;
+};
+
+int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
+               uint32_t filter_opt, uint32_t filter_bits_opt, TableBlob *out);
+void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dev_base);
+
 // Scan windows whose start x lies in [x_begin, x_end) of a text of n bytes
 // (bytes up to min(n, x_end + lmax - 1) must be resident); adds to d_info.
 int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
@@ -126,6 +140,12 @@ int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x
 
 int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);
+
+// Sort keys[0 .. d_info[0]) ascending over the 8-bit digits at the given bit
+// shifts (least significant first).
+int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, uint64_t *d_keys,
+                       uint64_t capacity, const uint64_t *d_info, void *d_ws, uint64_t ws_bytes,
+                       cudaStream_t stream);
 
 uint64_t sort_workspace_bytes(uint64_t capacity);
 

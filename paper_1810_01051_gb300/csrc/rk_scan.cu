@@ -31,8 +31,7 @@
 // All waits are bounded; on a timeout the kernel records RK_ETIMEOUT in
 // d_info[1], stops issuing copies, waits (bounded) for its copies in flight
 // and returns.
-#include "rk_internal.cuh"
-#include "rk_layout.cuh"
+#include "rk_scan_body.cuh"
 
 namespace rk {
 namespace {
@@ -53,198 +52,6 @@ struct ScanParams {
     unsigned long long *info;
     uint32_t tile, stages, halo, warps, s2_smem;
 };
-
-// 8 bytes starting at any position of a 16-byte aligned shared buffer,
-// little-endian (byte i of the window in bits 8i..8i+7).
-__device__ __forceinline__ uint64_t ld8(const uint8_t *buf, uint32_t pos) {
-    uint32_t a = pos & ~7u, s = (pos & 7u) * 8u;
-    uint64_t lo = *reinterpret_cast<const uint64_t *>(buf + a);
-    uint64_t hi = *reinterpret_cast<const uint64_t *>(buf + a + 8);
-    return s ? (lo >> s) | (hi << (64u - s)) : lo;
-}
-
-// Rabin hash of buf[pos .. pos+L) mod 2^61-1 with B = 2^k.
-__device__ __forceinline__ uint64_t window_hash(const uint8_t *buf, uint32_t pos, uint32_t L,
-                                               uint32_t k) {
-    if (k == 8) {
-        // 8-byte blocks: the block's big-endian value, and 256^8 = 2^64 = 2^3 (mod p).
-        uint32_t r = ((L - 1u) & 7u) + 1u;  // leading partial block, 1..8 bytes
-        uint64_t h = fold61(bswap64(ld8(buf, pos)) >> (64u - 8u * r));
-        for (uint32_t i = r; i < L; i += 8)
-            h = addmod61(rotl61(h, 3), fold61(bswap64(ld8(buf, pos + i))));
-        return h;
-    }
-    uint64_t h = 0;
-    for (uint32_t i = 0; i < L; ++i) {
-        h = rotl61(h, k) + buf[pos + i];
-        if (h >= kP61) h -= kP61;
-    }
-    return h;
-}
-
-// pat: 8-byte aligned, zero padded to a multiple of 8 (shared or global).
-__device__ __forceinline__ bool verify(const uint8_t *buf, uint32_t pos, const uint8_t *pat,
-                                       uint32_t L) {
-    for (uint32_t i = 0; i < L; i += 8) {
-        uint64_t d = ld8(buf, pos + i) ^ *reinterpret_cast<const uint64_t *>(pat + i);
-        uint32_t rem = L - i;
-        if (rem < 8) d &= (1ull << (8u * rem)) - 1ull;
-        if (d) return false;
-    }
-    return true;
-}
-
-// Survivor-stage tables, as generic pointers into shared or global memory.
-struct S2 {
-    const GramSlot *grams;
-    const uint32_t *gram_lens;
-    const uint2 *group_hdr;
-    const GroupSlot *slots;
-    const uint32_t *group_pids;
-    const uint8_t *pbytes;
-    const uint64_t *poff;
-    const uint32_t *lengths;
-};
-
-template <class T>
-__device__ __forceinline__ const T *rebase(const T *p, const uint8_t *from, const uint8_t *to) {
-    return reinterpret_cast<const T *>(to + (reinterpret_cast<const uint8_t *>(p) - from));
-}
-
-struct WarpCtx {
-    uint32_t *mcount;  // this warp's buffered-match counter
-    uint64_t *mbuf;    // this warp's match buffer
-    uint64_t *keys;
-    uint64_t capacity;
-    unsigned long long *info;
-};
-
-__device__ __forceinline__ void emit(const WarpCtx &w, uint64_t key) {
-    uint32_t s = atomicAdd(w.mcount, 1u);
-    if (s < kMatchCap) {
-        w.mbuf[s] = key;
-    } else {  // buffer full: append directly
-        unsigned long long g = atomicAdd(&w.info[0], 1ull);
-        if (g < w.capacity) w.keys[g] = key;
-    }
-}
-
-// Warp-converged: move the buffered matches to the output with one atomic.
-__device__ __forceinline__ void flush(const WarpCtx &w, uint32_t lane) {
-    __syncwarp();
-    uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kMatchCap);
-    if (cnt) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&w.info[0], (unsigned long long)cnt);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        for (uint32_t i = lane; i < cnt; i += 32)
-            if (base + i < w.capacity) w.keys[base + i] = w.mbuf[i];
-    }
-    __syncwarp();
-    if (lane == 0) *reinterpret_cast<volatile uint32_t *>(w.mcount) = 0;
-    __syncwarp();
-}
-
-// Probe the length-L group with the window's hash; verify and emit.
-__device__ __forceinline__ void probe_length(const S2 &s2, uint32_t base_log2, const WarpCtx &w,
-                                             const uint8_t *buf, uint32_t pos, uint64_t x,
-                                             uint32_t L) {
-    const uint2 hdr = s2.group_hdr[L];
-    if (hdr.y == 0) return;
-    const uint64_t h = window_hash(buf, pos, L, base_log2);
-    const uint64_t mask = (1ull << hdr.y) - 1ull;
-    uint64_t idx = (h * kGroupMult) >> (64u - hdr.y);
-    for (;;) {
-        const GroupSlot s = s2.slots[hdr.x + idx];
-        if (s.count == 0) return;
-        if (s.h == h) {
-            for (uint32_t j = 0; j < s.count; ++j) {
-                const uint32_t pid = s2.group_pids[s.first + j];
-                if (verify(buf, pos, s2.pbytes + s2.poff[pid], L))
-                    emit(w, ((uint64_t)pid << RK_KEY_OFFSET_BITS) | x);
-            }
-            return;
-        }
-        idx = (idx + 1) & mask;
-    }
-}
-
-// Stage 2 for one window at buffer position pos.
-template <int MODE>
-__device__ __forceinline__ void process_window(const ScanParams &P, const S2 &s2,
-                                               const WarpCtx &w, const uint8_t *buf,
-                                               uint32_t pos, uint64_t u0) {
-    const uint64_t ua = u0 + pos;
-    if (ua < P.mis + P.x_begin || ua >= P.mis + P.x_end) return;
-    const uint64_t x = ua - P.mis;
-    const DevTable &T = P.tab;
-    if (MODE == kFilterNone) {
-        for (uint32_t i = 0; i < T.n_lengths; ++i) {
-            const uint32_t L = s2.lengths[i];
-            if (x + L > P.n) break;
-            probe_length(s2, T.base_log2, w, buf, pos, x, L);
-        }
-        return;
-    }
-    const uint64_t v = ld8(buf, pos);  // window bytes 0..7, little-endian
-    const uint32_t key = T.q == 4 ? (uint32_t)v : (uint32_t)v & ((1u << (8u * T.q)) - 1u);
-    const uint32_t gmask = (1u << T.gram_bits) - 1u;
-    uint32_t idx = (key * kGramMult) >> (32u - T.gram_bits);
-    for (;;) {
-        const GramSlot g = s2.grams[idx];
-        if (g.count == 0) return;  // a false positive of the bit set
-        if (g.key == key) {
-            // patterns of length >= q + 4 need bytes q..q+3 in the fingerprint set
-            const bool ext_ok = (g.ext >> ext_bit((uint32_t)(v >> (8u * T.q)))) & 1u;
-            for (uint32_t j = 0; j < g.count; ++j) {
-                const uint32_t L = s2.gram_lens[g.first + j];
-                if (x + L > P.n) break;  // lengths ascend
-                if (L >= T.q + 4 && !ext_ok) break;
-                probe_length(s2, T.base_log2, w, buf, pos, x, L);
-            }
-            return;
-        }
-        idx = (idx + 1) & gmask;
-    }
-}
-
-// Stage 1 for one 16-byte chunk, given its words v and the next chunk's first
-// word v4: bit (15 - j) of the result is set when window j may start a match.
-template <int MODE, bool Q4>
-__device__ __forceinline__ uint32_t stage1(const uint4 v, const uint32_t v4, const uint8_t *sfilt,
-                                           uint32_t fmask, uint32_t lane4, uint32_t qmask) {
-    if (MODE == kFilterNone) return 0xFFFFu;
-    const uint32_t wd[5] = {v.x, v.y, v.z, v.w, v4};
-    // four independent 4-bit accumulators keep the dependency chains short
-    uint32_t acc[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        // bytes j..j+3 of the chunk as a little-endian word: the window's prefix
-        uint32_t g = (j & 3) == 0 ? wd[j >> 2]
-                                  : __funnelshift_r(wd[j >> 2], wd[(j >> 2) + 1], 8 * (j & 3));
-        if (!Q4) g &= qmask;
-        const uint32_t hh = __umulhi(g, kFilterMult);
-        const uint32_t a = MODE == kFilterReplicated ? ((hh & fmask) | lane4) : ((hh >> 3) & fmask);
-        const uint32_t word = *reinterpret_cast<const uint32_t *>(sfilt + a);
-        const uint32_t rot = __funnelshift_r(word, word, hh);  // bucket bit -> bit 31
-        acc[j >> 2] = __funnelshift_l(rot, acc[j >> 2], 1);    // acc = acc << 1 | bit
-    }
-    return (acc[0] << 12) | (acc[1] << 8) | (acc[2] << 4) | acc[3];
-}
-
-struct Chunk {
-    uint4 v;
-    uint32_t v4;
-};
-
-// Words of chunk c (clamped into the tile so the read stays in its buffer).
-__device__ __forceinline__ Chunk load_chunk(const uint8_t *buf, uint32_t c, uint32_t last) {
-    c = min(c, last);
-    Chunk k;
-    k.v = *reinterpret_cast<const uint4 *>(buf + 16u * c);
-    k.v4 = *reinterpret_cast<const uint32_t *>(buf + 16u * c + 16u);
-    return k;
-}
 
 // MAXW: most consumer warps this instance is launched with; the register
 // budget per thread follows from (MAXW + 1) warps per SM.  S2S: the
@@ -321,25 +128,24 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     }
 
     // -------------------------------------- consumer warps
-    S2 s2;
-    {
-        const DevTable &T = P.tab;
-        const uint8_t *from = T.s2_base;
-        const uint8_t *to = S2S ? ss2 : T.s2_base;
-        s2.grams = rebase(T.grams, from, to);
-        s2.gram_lens = rebase(T.gram_lens, from, to);
-        s2.group_hdr = rebase(T.group_hdr, from, to);
-        s2.slots = rebase(T.slots, from, to);
-        s2.group_pids = rebase(T.group_pids, from, to);
-        s2.pbytes = rebase(T.pbytes, from, to);
-        s2.poff = rebase(T.poff, from, to);
-        s2.lengths = rebase(T.lengths, from, to);
-    }
+    WinCtx C;
+    C.s2 = make_s2(P.tab, S2S ? ss2 : P.tab.s2_base);
+    C.lo = P.mis + P.x_begin;
+    C.hi = P.mis + P.x_end;
+    C.mis = P.mis;
+    C.n = P.n;
+    C.key_prefix = 0;
+    C.pid_shift = RK_KEY_OFFSET_BITS;
+    C.q = P.tab.q;
+    C.gram_bits = P.tab.gram_bits;
+    C.base_log2 = P.tab.base_log2;
+    C.n_lengths = P.tab.n_lengths;
     uint16_t *q = queues + warp * kQueueCap;
     WarpCtx w{mcount + warp, mbuf + (size_t)warp * kMatchCap, P.keys, P.capacity, P.info};
     const uint32_t lane4 = lane << 2;
     const uint32_t fmask = P.tab.filter_mask;
     const uint32_t qmask = P.tab.q == 4 ? 0xFFFFFFFFu : (1u << (8u * P.tab.q)) - 1u;
+    const uint32_t last = P.tile / 16u - 1u;
 
     for (uint64_t i = 0; i < my_tiles; ++i) {
         const uint32_t s = (uint32_t)(i % P.stages);
@@ -351,66 +157,10 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         const uint8_t *buf = stage0 + (size_t)s * lay.stage_stride;
         const uint64_t t = blockIdx.x + i * gridDim.x;
         const uint64_t u0 = P.u_first + t * P.tile;
-        const uint64_t wend = min(u0 + P.tile, P.mis + P.x_end);
+        const uint64_t wend = min(u0 + P.tile, C.hi);
         const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
-
-        uint32_t qn = 0;  // warp-uniform queue length (< 32 between rounds)
-        // Each lane takes chunks c0 + lane and c0 + 32 + lane (32 windows);
-        // the next pair's words are loaded before this pair is tested.
-        const uint32_t last = P.tile / 16u - 1u;
-        const uint32_t step = nw * 64u;
-        uint32_t c0 = warp * 64u;
-        Chunk ka = load_chunk(buf, c0 + lane, last), kb = load_chunk(buf, c0 + 32u + lane, last);
-        while (c0 < nchunks) {
-            const uint32_t ca = c0 + lane, cb = c0 + 32u + lane;
-            const Chunk na = load_chunk(buf, ca + step, last), nb = load_chunk(buf, cb + step, last);
-            uint32_t m = 0;
-            if (ca < nchunks) m = stage1<MODE, Q4>(ka.v, ka.v4, sfilt, fmask, lane4, qmask);
-            if (cb < nchunks) m |= stage1<MODE, Q4>(kb.v, kb.v4, sfilt, fmask, lane4, qmask) << 16;
-            ka = na;
-            kb = nb;
-            c0 += step;
-            if (__ballot_sync(0xffffffffu, m != 0) == 0) continue;
-            // bit b of m: window 15 - (b & 15) of chunk (b < 16 ? ca : cb)
-            const uint32_t cnt = __popc(m);
-            uint32_t incl = cnt;
-#pragma unroll
-            for (uint32_t d = 1; d < 32; d <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += o;
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            if (qn + total <= kQueueCap) {
-                uint32_t at = qn + incl - cnt;
-                while (m) {
-                    const uint32_t b = 31u - __clz(m);
-                    m &= ~(1u << b);
-                    q[at++] = (uint16_t)(16u * (b < 16 ? ca : cb) + (15u - (b & 15u)));
-                }
-                qn += total;
-                __syncwarp();
-                // full rounds: one queued window per lane
-                while (qn >= 32) {
-                    qn -= 32;
-                    process_window<MODE>(P, s2, w, buf, q[qn + lane], u0);
-                    __syncwarp();
-                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32)
-                        flush(w, lane);
-                }
-            } else {
-                // more survivors than the queue holds (very dense matches):
-                // each lane works through its own
-                while (m) {
-                    const uint32_t b = 31u - __clz(m);
-                    m &= ~(1u << b);
-                    process_window<MODE>(P, s2, w, buf,
-                                         16u * (b < 16 ? ca : cb) + (15u - (b & 15u)), u0);
-                }
-                flush(w, lane);
-            }
-        }
-        if (lane < qn) process_window<MODE>(P, s2, w, buf, q[lane], u0);
-        flush(w, lane);
+        consume_tile<MODE, Q4>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4, qmask, warp,
+                               nw, lane);
         if (lane == 0) mbar_arrive(&empty[s]);
     }
     flush(w, lane);

@@ -1,0 +1,295 @@
+// Device code that processes one staged text tile: the per-window prefilter
+// (stage 1), the per-warp survivor queue, and for survivors the Rabin hash
+// mod 2^61 - 1 at each candidate pattern length (A2), the probe of that
+// length's table (A3), the byte comparison (A4) and buffered emission (A5).
+// Shared by the single-text scan kernel and the batch kernel.
+#pragma once
+
+#include "rk_internal.cuh"
+#include "rk_layout.cuh"
+
+namespace rk {
+
+// 8 bytes starting at any position of a 16-byte aligned shared buffer,
+// little-endian (byte i of the window in bits 8i..8i+7).
+__device__ __forceinline__ uint64_t ld8(const uint8_t *buf, uint32_t pos) {
+    uint32_t a = pos & ~7u, s = (pos & 7u) * 8u;
+    uint64_t lo = *reinterpret_cast<const uint64_t *>(buf + a);
+    uint64_t hi = *reinterpret_cast<const uint64_t *>(buf + a + 8);
+    return s ? (lo >> s) | (hi << (64u - s)) : lo;
+}
+
+// Rabin hash of buf[pos .. pos+L) mod 2^61-1 with B = 2^k.
+__device__ __forceinline__ uint64_t window_hash(const uint8_t *buf, uint32_t pos, uint32_t L,
+                                               uint32_t k) {
+    if (k == 8) {
+        // 8-byte blocks: the block's big-endian value, and 256^8 = 2^64 = 2^3 (mod p).
+        uint32_t r = ((L - 1u) & 7u) + 1u;  // leading partial block, 1..8 bytes
+        uint64_t h = fold61(bswap64(ld8(buf, pos)) >> (64u - 8u * r));
+        for (uint32_t i = r; i < L; i += 8)
+            h = addmod61(rotl61(h, 3), fold61(bswap64(ld8(buf, pos + i))));
+        return h;
+    }
+    uint64_t h = 0;
+    for (uint32_t i = 0; i < L; ++i) {
+        h = rotl61(h, k) + buf[pos + i];
+        if (h >= kP61) h -= kP61;
+    }
+    return h;
+}
+
+// pat: 8-byte aligned, zero padded to a multiple of 8 (shared or global).
+__device__ __forceinline__ bool verify(const uint8_t *buf, uint32_t pos, const uint8_t *pat,
+                                       uint32_t L) {
+    for (uint32_t i = 0; i < L; i += 8) {
+        uint64_t d = ld8(buf, pos + i) ^ *reinterpret_cast<const uint64_t *>(pat + i);
+        uint32_t rem = L - i;
+        if (rem < 8) d &= (1ull << (8u * rem)) - 1ull;
+        if (d) return false;
+    }
+    return true;
+}
+
+// Survivor-stage tables, as pointers into shared or global memory.
+struct S2 {
+    const GramSlot *grams;
+    const uint32_t *gram_lens;
+    const uint2 *group_hdr;
+    const GroupSlot *slots;
+    const uint32_t *group_pids;
+    const uint8_t *pbytes;
+    const uint64_t *poff;
+    const uint32_t *lengths;
+};
+
+template <class T>
+__device__ __forceinline__ const T *rebase(const T *p, const uint8_t *from, const uint8_t *to) {
+    return reinterpret_cast<const T *>(to + (reinterpret_cast<const uint8_t *>(p) - from));
+}
+
+// The survivor tables of `T`, moved to `to` when they were copied there.
+__device__ __forceinline__ S2 make_s2(const DevTable &T, const uint8_t *to) {
+    S2 s;
+    const uint8_t *from = T.s2_base;
+    s.grams = rebase(T.grams, from, to);
+    s.gram_lens = rebase(T.gram_lens, from, to);
+    s.group_hdr = rebase(T.group_hdr, from, to);
+    s.slots = rebase(T.slots, from, to);
+    s.group_pids = rebase(T.group_pids, from, to);
+    s.pbytes = rebase(T.pbytes, from, to);
+    s.poff = rebase(T.poff, from, to);
+    s.lengths = rebase(T.lengths, from, to);
+    return s;
+}
+
+// What the survivor stage needs to know about the text being scanned.
+struct WinCtx {
+    S2 s2;
+    uint64_t lo, hi;      // buffer positions (from the aligned base) of the windows scanned
+    uint64_t mis;         // buffer position of text byte 0
+    uint64_t n;           // text length
+    uint64_t key_prefix;  // or-ed into every key
+    uint32_t pid_shift;   // bit position of the pattern id in a key
+    uint32_t q, gram_bits, base_log2, n_lengths;
+};
+
+struct WarpCtx {
+    uint32_t *mcount;  // this warp's buffered-match counter
+    uint64_t *mbuf;    // this warp's match buffer
+    uint64_t *keys;
+    uint64_t capacity;
+    unsigned long long *info;
+};
+
+__device__ __forceinline__ void emit(const WarpCtx &w, uint64_t key) {
+    uint32_t s = atomicAdd(w.mcount, 1u);
+    if (s < kMatchCap) {
+        w.mbuf[s] = key;
+    } else {  // buffer full: append directly
+        unsigned long long g = atomicAdd(&w.info[0], 1ull);
+        if (g < w.capacity) w.keys[g] = key;
+    }
+}
+
+// Warp-converged: move the buffered matches to the output with one atomic.
+__device__ __forceinline__ void flush(const WarpCtx &w, uint32_t lane) {
+    __syncwarp();
+    uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kMatchCap);
+    if (cnt) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&w.info[0], (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t i = lane; i < cnt; i += 32)
+            if (base + i < w.capacity) w.keys[base + i] = w.mbuf[i];
+    }
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile uint32_t *>(w.mcount) = 0;
+    __syncwarp();
+}
+
+// Probe the length-L group with the window's hash; verify and emit.
+__device__ __forceinline__ void probe_length(const WinCtx &C, const WarpCtx &w,
+                                             const uint8_t *buf, uint32_t pos, uint64_t x,
+                                             uint32_t L) {
+    const uint2 hdr = C.s2.group_hdr[L];
+    if (hdr.y == 0) return;
+    const uint64_t h = window_hash(buf, pos, L, C.base_log2);
+    const uint64_t mask = (1ull << hdr.y) - 1ull;
+    uint64_t idx = (h * kGroupMult) >> (64u - hdr.y);
+    for (;;) {
+        const GroupSlot s = C.s2.slots[hdr.x + idx];
+        if (s.count == 0) return;
+        if (s.h == h) {
+            for (uint32_t j = 0; j < s.count; ++j) {
+                const uint32_t pid = C.s2.group_pids[s.first + j];
+                if (verify(buf, pos, C.s2.pbytes + C.s2.poff[pid], L))
+                    emit(w, C.key_prefix | ((uint64_t)pid << C.pid_shift) | x);
+            }
+            return;
+        }
+        idx = (idx + 1) & mask;
+    }
+}
+
+// Stage 2 for one window at buffer position pos of the tile starting at u0.
+template <int MODE>
+__device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w,
+                                               const uint8_t *buf, uint32_t pos, uint64_t u0) {
+    const uint64_t ua = u0 + pos;
+    if (ua < C.lo || ua >= C.hi) return;
+    const uint64_t x = ua - C.mis;
+    if (MODE == kFilterNone) {
+        for (uint32_t i = 0; i < C.n_lengths; ++i) {
+            const uint32_t L = C.s2.lengths[i];
+            if (x + L > C.n) break;
+            probe_length(C, w, buf, pos, x, L);
+        }
+        return;
+    }
+    const uint64_t v = ld8(buf, pos);  // window bytes 0..7, little-endian
+    const uint32_t key = C.q == 4 ? (uint32_t)v : (uint32_t)v & ((1u << (8u * C.q)) - 1u);
+    const uint32_t gmask = (1u << C.gram_bits) - 1u;
+    uint32_t idx = (key * kGramMult) >> (32u - C.gram_bits);
+    for (;;) {
+        const GramSlot g = C.s2.grams[idx];
+        if (g.count == 0) return;  // a false positive of the bit set
+        if (g.key == key) {
+            // patterns of length >= q + 4 need bytes q..q+3 in the fingerprint set
+            const bool ext_ok = (g.ext >> ext_bit((uint32_t)(v >> (8u * C.q)))) & 1u;
+            for (uint32_t j = 0; j < g.count; ++j) {
+                const uint32_t L = C.s2.gram_lens[g.first + j];
+                if (x + L > C.n) break;  // lengths ascend
+                if (L >= C.q + 4 && !ext_ok) break;
+                probe_length(C, w, buf, pos, x, L);
+            }
+            return;
+        }
+        idx = (idx + 1) & gmask;
+    }
+}
+
+// Stage 1 for one 16-byte chunk, given its words v and the next chunk's first
+// word v4: bit (15 - j) of the result is set when window j may start a match.
+template <int MODE, bool Q4>
+__device__ __forceinline__ uint32_t stage1(const uint4 v, const uint32_t v4, const uint8_t *sfilt,
+                                           uint32_t fmask, uint32_t lane4, uint32_t qmask) {
+    if (MODE == kFilterNone) return 0xFFFFu;
+    const uint32_t wd[5] = {v.x, v.y, v.z, v.w, v4};
+    // four independent 4-bit accumulators keep the dependency chains short
+    uint32_t acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        // bytes j..j+3 of the chunk as a little-endian word: the window's prefix
+        uint32_t g = (j & 3) == 0 ? wd[j >> 2]
+                                  : __funnelshift_r(wd[j >> 2], wd[(j >> 2) + 1], 8 * (j & 3));
+        if (!Q4) g &= qmask;
+        const uint32_t hh = __umulhi(g, kFilterMult);
+        const uint32_t a = MODE == kFilterReplicated ? ((hh & fmask) | lane4) : ((hh >> 3) & fmask);
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(sfilt + a);
+        const uint32_t rot = __funnelshift_r(word, word, hh);  // bucket bit -> bit 31
+        acc[j >> 2] = __funnelshift_l(rot, acc[j >> 2], 1);    // acc = acc << 1 | bit
+    }
+    return (acc[0] << 12) | (acc[1] << 8) | (acc[2] << 4) | acc[3];
+}
+
+struct Chunk {
+    uint4 v;
+    uint32_t v4;
+};
+
+// Words of chunk c (clamped into the tile so the read stays in its buffer).
+__device__ __forceinline__ Chunk load_chunk(const uint8_t *buf, uint32_t c, uint32_t last) {
+    c = min(c, last);
+    Chunk k;
+    k.v = *reinterpret_cast<const uint4 *>(buf + 16u * c);
+    k.v4 = *reinterpret_cast<const uint32_t *>(buf + 16u * c + 16u);
+    return k;
+}
+
+// One consumer warp's share of a staged tile: chunks warp*64 + {lane, 32 +
+// lane} + k * nw * 64 (32 windows per lane per round), survivors queued per
+// warp and processed one window per lane, matches flushed at the end.
+//   buf: the tile's shared buffer; u0: its buffer position; nchunks: 16-byte
+//   chunks holding window starts; last: highest chunk index of a full tile.
+template <int MODE, bool Q4>
+__device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, uint16_t *q,
+                                             const uint8_t *buf, uint64_t u0, uint32_t nchunks,
+                                             uint32_t last, const uint8_t *sfilt, uint32_t fmask,
+                                             uint32_t lane4, uint32_t qmask, uint32_t warp,
+                                             uint32_t nw, uint32_t lane) {
+    uint32_t qn = 0;  // warp-uniform queue length (< 32 between rounds)
+    const uint32_t step = nw * 64u;
+    uint32_t c0 = warp * 64u;
+    Chunk ka = load_chunk(buf, c0 + lane, last), kb = load_chunk(buf, c0 + 32u + lane, last);
+    while (c0 < nchunks) {
+        const uint32_t ca = c0 + lane, cb = c0 + 32u + lane;
+        const Chunk na = load_chunk(buf, ca + step, last), nb = load_chunk(buf, cb + step, last);
+        uint32_t m = 0;
+        if (ca < nchunks) m = stage1<MODE, Q4>(ka.v, ka.v4, sfilt, fmask, lane4, qmask);
+        if (cb < nchunks) m |= stage1<MODE, Q4>(kb.v, kb.v4, sfilt, fmask, lane4, qmask) << 16;
+        ka = na;
+        kb = nb;
+        c0 += step;
+        if (__ballot_sync(0xffffffffu, m != 0) == 0) continue;
+        // bit b of m: window 15 - (b & 15) of chunk (b < 16 ? ca : cb)
+        const uint32_t cnt = __popc(m);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (qn + total <= kQueueCap) {
+            uint32_t at = qn + incl - cnt;
+            while (m) {
+                const uint32_t b = 31u - __clz(m);
+                m &= ~(1u << b);
+                q[at++] = (uint16_t)(16u * (b < 16 ? ca : cb) + (15u - (b & 15u)));
+            }
+            qn += total;
+            __syncwarp();
+            // full rounds: one queued window per lane
+            while (qn >= 32) {
+                qn -= 32;
+                process_window<MODE>(C, w, buf, q[qn + lane], u0);
+                __syncwarp();
+                if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32)
+                    flush(w, lane);
+            }
+        } else {
+            // more survivors than the queue holds (very dense matches):
+            // each lane works through its own
+            while (m) {
+                const uint32_t b = 31u - __clz(m);
+                m &= ~(1u << b);
+                process_window<MODE>(C, w, buf, 16u * (b < 16 ? ca : cb) + (15u - (b & 15u)), u0);
+            }
+            flush(w, lane);
+        }
+    }
+    if (lane < qn) process_window<MODE>(C, w, buf, q[lane], u0);
+    flush(w, lane);
+}
+
+}  // namespace rk

@@ -197,10 +197,11 @@ uint32_t bits_for(uint64_t max_value) {
 
 uint64_t sort_workspace_bytes(uint64_t capacity) { return sort_ws_bytes(capacity); }
 
-int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
-                const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream) {
-    if (capacity < 2 || n == 0 || t->dev.n_patterns == 0) return RK_OK;
-    if (ws_bytes < sort_ws_bytes(capacity)) return RK_EINVAL;
+int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, uint64_t *d_keys,
+                       uint64_t capacity, const uint64_t *d_info, void *d_ws, uint64_t ws_bytes,
+                       cudaStream_t stream) {
+    if (capacity < 2 || nshift == 0) return RK_OK;
+    if (nshift > kMaxSortPasses || ws_bytes < sort_ws_bytes(capacity)) return RK_EINVAL;
     const SortWsLayout L = sort_ws_layout(capacity);
     uint8_t *ws = reinterpret_cast<uint8_t *>(d_ws);
     uint64_t *tmp = reinterpret_cast<uint64_t *>(ws + L.tmp_off);
@@ -209,31 +210,37 @@ int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capaci
     uint64_t *status = reinterpret_cast<uint64_t *>(ws + L.status_off);
     unsigned long long *info =
         reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(d_info));
-
     Shifts sh{};
-    const uint32_t ob = bits_for(n - 1), pb = bits_for(t->dev.n_patterns - 1);
-    for (uint32_t s = 0; s < ob; s += 8) sh.s[sh.n++] = s;
-    for (uint32_t s = 0; s < pb; s += 8) sh.s[sh.n++] = RK_KEY_OFFSET_BITS + s;
-    if (sh.n == 0) return RK_OK;
+    for (uint32_t i = 0; i < nshift; ++i) sh.s[sh.n++] = shifts[i];
 
     if (cudaMemsetAsync(ws + L.ctrl_off, 0, L.status_off - L.ctrl_off, stream) != cudaSuccess)
         return RK_ECUDA;
-    const uint32_t grid = (uint32_t)t->sm_count * 4;
+    const uint32_t grid = (uint32_t)sm_count * 4;
     const uint64_t tiles = L.tiles;
     rk_sort_hist_kernel<<<grid, kThreads, 0, stream>>>(d_keys, info, capacity, sh, ghist, status,
                                                        tiles);
     for (uint32_t p = 0; p < sh.n; ++p) {
         const uint64_t *src = (p & 1) ? tmp : d_keys;
         uint64_t *dst = (p & 1) ? d_keys : tmp;
-        const uint32_t pgrid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)t->sm_count * 8);
+        const uint32_t pgrid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * 8);
         rk_sort_pass_kernel<<<pgrid, kThreads, 0, stream>>>(
             src, dst, info, capacity, sh.s[p], ghist + p * 256, status + (uint64_t)p * tiles * 256,
             counters + p);
     }
     if (sh.n & 1)
-        rk_sort_copy_kernel<<<(uint32_t)t->sm_count * 4, 256, 0, stream>>>(tmp, d_keys, info,
-                                                                           capacity);
+        rk_sort_copy_kernel<<<(uint32_t)sm_count * 4, 256, 0, stream>>>(tmp, d_keys, info, capacity);
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
+int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
+                const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream) {
+    if (n == 0 || t->dev.n_patterns == 0) return RK_OK;
+    uint32_t shifts[kMaxSortPasses], ns = 0;
+    const uint32_t ob = bits_for(n - 1), pb = bits_for(t->dev.n_patterns - 1);
+    for (uint32_t s = 0; s < ob; s += 8) shifts[ns++] = s;
+    for (uint32_t s = 0; s < pb; s += 8) shifts[ns++] = RK_KEY_OFFSET_BITS + s;
+    return launch_sort_shifts(t->sm_count, shifts, ns, d_keys, capacity, d_info, d_ws, ws_bytes,
+                              stream);
 }
 
 }  // namespace rk

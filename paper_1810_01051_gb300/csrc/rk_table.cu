@@ -82,27 +82,12 @@ extern "C" const char *rk_strerror(int status) {
     }
 }
 
-extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
-                        const rk_build_opts *opts, rk_table **out) {
-    if (!out) return RK_EINVAL;
-    *out = nullptr;
-    if (k > RK_MAX_PATTERNS) return RK_EINVAL;
-    if (k > 0 && (!patterns || !lens)) return RK_EINVAL;
-    rk_build_opts o{};
-    if (opts) o = *opts;
-    uint32_t base_log2 = o.base_log2 ? o.base_log2 : 8;
-    if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
-    if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
-    uint32_t warps = o.warps ? o.warps : 16;
-    // default: 48 KiB tiles (three 16 KiB rounds of 16 warps), two in flight
-    uint32_t tile = o.tile_bytes ? o.tile_bytes : 49152;
-    uint32_t stages = o.stages ? o.stages : 2;
-    uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
-    // survivor positions within a tile are 16-bit
-    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > kMaxTileBytes ||
-        stages < 2 || stages > 8 || cps < 1 || cps > 8)
-        return RK_EINVAL;
+namespace rk {
 
+// Serialise the pattern table of one pattern set into a host image; every
+// part is 256-byte aligned and the image ends on a 256-byte boundary.
+int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
+               uint32_t filter_opt, uint32_t filter_bits_opt, TableBlob *out) {
     // ---- patterns ---------------------------------------------------------
     std::vector<uint64_t> src_off(k), poff(k);
     std::vector<uint32_t> plen(k);
@@ -160,11 +145,11 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     }
 
     // ---- stage-1 bit set ---------------------------------------------------
-    uint32_t mode, fbits = o.filter_log2_bits;
-    if (o.filter == RK_FILTER_NONE) {
+    uint32_t mode, fbits = filter_bits_opt;
+    if (filter_opt == RK_FILTER_NONE) {
         mode = kFilterNone;
-    } else if (o.filter == RK_FILTER_REPLICATED ||
-               (o.filter == RK_FILTER_AUTO && D <= 256 && !fbits)) {
+    } else if (filter_opt == RK_FILTER_REPLICATED ||
+               (filter_opt == RK_FILTER_AUTO && D <= 256 && !fbits)) {
         mode = kFilterReplicated;
         if (!fbits) fbits = 14;
         if (fbits < 10 || fbits > 15) return RK_EINVAL;
@@ -257,6 +242,82 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     if (!lengths.empty()) memcpy(hb + o_lens, lengths.data(), lengths.size() * 4);
 
     if (b.bytes.size() - o_grams > 0xFFFFFFFFull) return RK_EINVAL;  // tables above 4 GiB
+    TableBlob &tb = *out;
+    tb.o_filter = o_filter;
+    tb.o_grams = o_grams;
+    tb.o_glens = o_glens;
+    tb.o_ghdr = o_ghdr;
+    tb.o_slots = o_slots;
+    tb.o_gpids = o_gpids;
+    tb.o_pbytes = o_pbytes;
+    tb.o_poff = o_poff;
+    tb.o_plen = o_plen;
+    tb.o_lens = o_lens;
+    DevTable &d = tb.meta;
+    d = DevTable{};
+    d.filter_bytes = (uint32_t)(fimg.size() * 4);
+    d.filter_mode = mode;
+    d.filter_mask = fmask;
+    d.q = q;
+    d.gram_bits = gram_bits;
+    d.n_lengths = (uint32_t)lengths.size();
+    d.n_patterns = k;
+    d.lmin = lmin;
+    d.lmax = lmax;
+    d.base_log2 = base_log2;
+    d.s2_bytes = (uint32_t)(b.bytes.size() - o_grams);
+    tb.n_grams = D;
+    tb.filter_log2_bits = mode == kFilterNone ? 0 : fbits;
+    tb.bytes = std::move(b.bytes);
+    return RK_OK;
+}
+
+// Point the device view of a table at its image placed at device address dm.
+void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dm) {
+    *d = b.meta;
+    d->filter = (const uint32_t *)(dm + b.o_filter);
+    d->grams = (const GramSlot *)(dm + b.o_grams);
+    d->gram_lens = (const uint32_t *)(dm + b.o_glens);
+    d->group_hdr = (const uint2 *)(dm + b.o_ghdr);
+    d->slots = (const GroupSlot *)(dm + b.o_slots);
+    d->group_pids = (const uint32_t *)(dm + b.o_gpids);
+    d->pbytes = dm + b.o_pbytes;
+    d->poff = (const uint64_t *)(dm + b.o_poff);
+    d->plen = (const uint32_t *)(dm + b.o_plen);
+    d->lengths = (const uint32_t *)(dm + b.o_lens);
+    d->s2_base = dm + b.o_grams;
+}
+
+}  // namespace rk
+
+extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
+                        const rk_build_opts *opts, rk_table **out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    if (k > RK_MAX_PATTERNS) return RK_EINVAL;
+    if (k > 0 && (!patterns || !lens)) return RK_EINVAL;
+    rk_build_opts o{};
+    if (opts) o = *opts;
+    uint32_t base_log2 = o.base_log2 ? o.base_log2 : 8;
+    if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
+    if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
+    uint32_t warps = o.warps ? o.warps : 16;
+    // default: 48 KiB tiles (three 16 KiB rounds of 16 warps), two in flight
+    uint32_t tile = o.tile_bytes ? o.tile_bytes : 49152;
+    uint32_t stages = o.stages ? o.stages : 2;
+    uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
+    // survivor positions within a tile are 16-bit
+    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > kMaxTileBytes ||
+        stages < 2 || stages > 8 || cps < 1 || cps > 8)
+        return RK_EINVAL;
+
+    TableBlob tb;
+    int rc = build_blob(patterns, lens, k, base_log2, o.filter, o.filter_log2_bits, &tb);
+    if (rc) return rc;
+    const uint32_t lmax = tb.meta.lmax;
+    const uint32_t fbytes = tb.meta.filter_bytes;
+    const uint64_t s2_total = tb.meta.s2_bytes;
+
     int dev = 0, sms = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RK_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -267,12 +328,10 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
 
     // ---- launch shape: shrink stages / tile until shared memory fits -------
     uint32_t halo = align_up(std::max<uint32_t>(lmax - 1, 1), 16);
-    uint32_t fbytes = (uint32_t)(fimg.size() * 4);
     uint32_t limit = (uint32_t)smem_optin / cps - 1024;  // room for static shared memory
     // The survivor-stage tables go to shared memory when they fit beside the
     // requested pipeline (or beside a two-stage one); otherwise they are read
     // from global memory (L2).
-    const uint64_t s2_total = b.bytes.size() - o_grams;
     uint32_t s2 = 0;
     if (s2_total <= limit) {
         if (smem_layout(fbytes, (uint32_t)s2_total, warps, stages, tile, halo).total <= limit) {
@@ -295,44 +354,22 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     if (!t) return RK_ENOMEM;
     t->device = dev;
     t->sm_count = sms;
-    if (cudaMalloc(&t->d_mem, b.bytes.size()) != cudaSuccess) {
+    if (cudaMalloc(&t->d_mem, tb.bytes.size()) != cudaSuccess) {
         delete t;
         cudaGetLastError();
         return RK_ENOMEM;
     }
-    t->d_bytes = b.bytes.size();
-    if (cudaMemcpy(t->d_mem, hb, b.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    t->d_bytes = tb.bytes.size();
+    if (cudaMemcpy(t->d_mem, tb.bytes.data(), tb.bytes.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
         cudaFree(t->d_mem);
         delete t;
         return RK_ECUDA;
     }
-    uint8_t *dm = (uint8_t *)t->d_mem;
-    DevTable &d = t->dev;
-    d.filter = (const uint32_t *)(dm + o_filter);
-    d.filter_bytes = fbytes;
-    d.filter_mode = mode;
-    d.filter_mask = fmask;
-    d.q = q;
-    d.grams = (const GramSlot *)(dm + o_grams);
-    d.gram_bits = gram_bits;
-    d.gram_lens = (const uint32_t *)(dm + o_glens);
-    d.group_hdr = (const uint2 *)(dm + o_ghdr);
-    d.slots = (const GroupSlot *)(dm + o_slots);
-    d.group_pids = (const uint32_t *)(dm + o_gpids);
-    d.pbytes = dm + o_pbytes;
-    d.poff = (const uint64_t *)(dm + o_poff);
-    d.plen = (const uint32_t *)(dm + o_plen);
-    d.lengths = (const uint32_t *)(dm + o_lens);
-    d.n_lengths = (uint32_t)lengths.size();
-    d.n_patterns = k;
-    d.lmin = lmin;
-    d.lmax = lmax;
-    d.base_log2 = base_log2;
-    d.s2_base = dm + o_grams;
-    d.s2_bytes = (uint32_t)s2_total;
+    bind_blob(&t->dev, tb, (const uint8_t *)t->d_mem);
     t->tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
-    t->n_grams = D;
-    t->filter_log2_bits = mode == kFilterNone ? 0 : fbits;
+    t->n_grams = tb.n_grams;
+    t->filter_log2_bits = tb.filter_log2_bits;
     t->filter_opt = o.filter;
     *out = t;
     return RK_OK;

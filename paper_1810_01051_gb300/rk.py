@@ -30,6 +30,9 @@ EXPORTS = [
     "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
     "rk_window_hashes_device", "rk_search_device_noalloc",
+    "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
+    "rk_batch_info_get", "rk_batch_set", "rk_batch_run", "rk_batch_results", "rk_batch_read",
+    "rk_batch_autotune",
 ]
 
 
@@ -50,6 +53,19 @@ class TableInfo(ctypes.Structure):
         "filter_log2_bits", "filter_smem_bytes", "n_grams", "warps", "tile_bytes", "stages",
         "ctas_per_sm", "halo_bytes", "smem_bytes", "sm_count", "device", "s2_smem_bytes")] + [
         ("device_bytes", ctypes.c_uint64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("max_items", ctypes.c_uint32), ("max_text_len", ctypes.c_uint64),
+                ("max_total_bytes", ctypes.c_uint64), ("capacity", ctypes.c_uint64)] + [
+        (n, ctypes.c_uint32) for n in ("warps", "tile_bytes", "stages", "ctas_per_sm",
+                                       "s2_in_smem")]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "offset_bits", "id_bits", "item_bits", "warps", "tile_bytes", "stages", "ctas_per_sm",
+        "s2_in_smem", "smem_bytes", "n_chunks", "max_chunks")]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -92,6 +108,26 @@ def load() -> ctypes.CDLL:
     L.rk_window_hashes_device.argtypes = [vp, u64, u32, u32, vp, vp]
     L.rk_search_device_noalloc.restype = ctypes.c_int
     L.rk_search_device_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+    L.rk_tableset_build.restype = ctypes.c_int
+    L.rk_tableset_build.argtypes = [u32, vp, vp, vp, ctypes.POINTER(BuildOpts), ctypes.POINTER(vp)]
+    L.rk_tableset_destroy.restype = None
+    L.rk_tableset_destroy.argtypes = [vp]
+    L.rk_batch_create.restype = ctypes.c_int
+    L.rk_batch_create.argtypes = [vp, ctypes.POINTER(BatchOpts), ctypes.POINTER(vp)]
+    L.rk_batch_destroy.restype = None
+    L.rk_batch_destroy.argtypes = [vp]
+    L.rk_batch_info_get.restype = ctypes.c_int
+    L.rk_batch_info_get.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    L.rk_batch_set.restype = ctypes.c_int
+    L.rk_batch_set.argtypes = [vp, u32, vp, vp, vp, vp]
+    L.rk_batch_run.restype = ctypes.c_int
+    L.rk_batch_run.argtypes = [vp, vp]
+    L.rk_batch_results.restype = ctypes.c_int
+    L.rk_batch_results.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.rk_batch_read.restype = ctypes.c_int
+    L.rk_batch_read.argtypes = [vp, vp, u64, vp, vp, vp]
+    L.rk_batch_autotune.restype = ctypes.c_int
+    L.rk_batch_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_double), vp]
     _lib = L
     return L
 
@@ -201,6 +237,95 @@ def rk_search_device_noalloc(table: int, d_text, n: int, d_keys, capacity: int, 
     _check(load().rk_search_device_noalloc(table, _ptr(d_text), n, _ptr(d_keys), capacity,
                                            _ptr(d_info), _stream(stream)),
            "rk_search_device_noalloc")
+
+
+# ------------------------------------------------------------------ batches
+
+def rk_tableset_build(tables: Sequence[Sequence[bytes]], base_log2: int = 0,
+                      filter: int = RK_FILTER_AUTO, filter_log2_bits: int = 0) -> int:
+    """One table per pattern list; returns the table-set handle."""
+    L = load()
+    per = np.array([len(t) for t in tables], dtype=np.uint32)
+    flat = [bytes(p) for t in tables for p in t]
+    lens = np.array([len(p) for p in flat] or [0], dtype=np.uint32)
+    cat = np.frombuffer(b"".join(flat) or b"\0", dtype=np.uint8).copy()
+    opts = BuildOpts(base_log2, filter, filter_log2_bits, 0, 0, 0, 0)
+    out = ctypes.c_void_p()
+    _check(L.rk_tableset_build(len(tables), cat.ctypes.data, lens.ctypes.data, per.ctypes.data,
+                               ctypes.byref(opts), ctypes.byref(out)), "rk_tableset_build")
+    return int(out.value)
+
+
+def rk_tableset_destroy(ts: int) -> None:
+    load().rk_tableset_destroy(ts)
+
+
+def rk_batch_create(ts: int, max_items: int, max_text_len: int, max_total_bytes: int,
+                    capacity: int, warps: int = 0, tile_bytes: int = 0, stages: int = 0,
+                    ctas_per_sm: int = 0, s2_in_smem: int = 0) -> int:
+    opts = BatchOpts(max_items, max_text_len, max_total_bytes, capacity, warps, tile_bytes,
+                     stages, ctas_per_sm, s2_in_smem)
+    out = ctypes.c_void_p()
+    _check(load().rk_batch_create(ts, ctypes.byref(opts), ctypes.byref(out)), "rk_batch_create")
+    return int(out.value)
+
+
+def rk_batch_destroy(b: int) -> None:
+    load().rk_batch_destroy(b)
+
+
+def rk_batch_info(b: int) -> dict:
+    info = BatchInfo()
+    _check(load().rk_batch_info_get(b, ctypes.byref(info)), "rk_batch_info_get")
+    return {name: getattr(info, name) for name, _ in BatchInfo._fields_}
+
+
+def rk_batch_set(b: int, table_of_item: Sequence[int], d_texts: Sequence, text_lens: Sequence[int],
+                 stream=None) -> None:
+    n = len(table_of_item)
+    tabs = np.asarray(table_of_item, dtype=np.uint32)
+    ptrs = np.array([_ptr(t) for t in d_texts] or [0], dtype=np.uint64)
+    lens = np.asarray(list(text_lens) or [0], dtype=np.uint64)
+    _check(load().rk_batch_set(b, n, tabs.ctypes.data if n else None, ptrs.ctypes.data,
+                               lens.ctypes.data, _stream(stream)), "rk_batch_set")
+
+
+def rk_batch_run(b: int, stream=None) -> None:
+    _check(load().rk_batch_run(b, _stream(stream)), "rk_batch_run")
+
+
+def rk_batch_results(b: int) -> Tuple[int, int, int]:
+    k, o, i = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().rk_batch_results(b, ctypes.byref(k), ctypes.byref(o), ctypes.byref(i)),
+           "rk_batch_results")
+    return int(k.value or 0), int(o.value or 0), int(i.value or 0)
+
+
+def rk_batch_read(b: int, n_items: int, key_cap: int, stream=None):
+    """(count, status, keys uint64[min(count, key_cap)], offsets uint64[n_items+1])."""
+    keys = np.empty(max(key_cap, 1), dtype=np.uint64)
+    offs = np.zeros(n_items + 1, dtype=np.uint64)
+    info = np.zeros(2, dtype=np.uint64)
+    _check(load().rk_batch_read(b, keys.ctypes.data, key_cap, offs.ctypes.data,
+                                info.ctypes.data, _stream(stream)), "rk_batch_read")
+    count, status = int(info[0]), int(info[1])
+    return count, status, keys[:min(count, key_cap)], offs
+
+
+def rk_batch_autotune(b: int, max_candidates: int = 0, reps: int = 3, stream=None) -> float:
+    best = ctypes.c_double(0)
+    _check(load().rk_batch_autotune(b, max_candidates, reps, ctypes.byref(best), _stream(stream)),
+           "rk_batch_autotune")
+    return best.value
+
+
+def unpack_batch_keys(keys: np.ndarray, offset_bits: int, id_bits: int):
+    """Split batch keys into (items, ids, offsets)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    offs = keys & np.uint64((1 << offset_bits) - 1)
+    ids = ((keys >> np.uint64(offset_bits)) & np.uint64((1 << id_bits) - 1)).astype(np.uint32)
+    items = (keys >> np.uint64(offset_bits + id_bits)).astype(np.uint32)
+    return items, ids, offs
 
 
 # ------------------------------------------------------------------ key packing

@@ -12,4 +12,6 @@ from .gen import (  # noqa: F401
     signature_set,
     random_small,
     make_config,
+    Batch,
+    batched,
 )

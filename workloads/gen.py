@@ -184,6 +184,48 @@ def random_small(seed: int, n: int, k: int, lmin: int, lmax: int,
                     dict(seed=seed, n=n, k=k, lmin=lmin, lmax=lmax, plants=plants))
 
 
+@dataclasses.dataclass
+class Batch:
+    """Many independent search problems: texts[i] is searched with tables[table_of[i]]."""
+
+    name: str
+    texts: List[np.ndarray]
+    tables: List[List[bytes]]
+    table_of: List[int]
+    params: dict
+
+    @property
+    def total_bytes(self) -> int:
+        return int(sum(t.size for t in self.texts))
+
+
+BATCH_ALPHABET = b"ABCDEFGHIJKLMNOPQRST"
+
+
+def batched(seed: int = 0x5EED0003, n_items: int = 4096, min_len: int = 1 << 10,
+            max_len: int = 1 << 24, k_min: int = 1, k_max: int = 256, lmin: int = 4,
+            lmax: int = 48, alphabet: bytes = BATCH_ALPHABET, density: float = 1e-5) -> Batch:
+    """Batched search: n_items texts with log-uniform lengths in [min_len,
+    max_len] over `alphabet`, each with its own set of U{k_min..k_max}
+    patterns of lengths U{lmin..lmax} over the same alphabet, each pattern
+    planted round(density * len) times.  Draw order: all text lengths, then per
+    item: text, pattern count, pattern lengths and bytes, plant offsets."""
+    rng = np.random.default_rng(seed)
+    lens = np.exp(rng.uniform(np.log(min_len), np.log(max_len), n_items)).astype(np.int64)
+    texts, tables = [], []
+    for n in lens:
+        n = int(n)
+        text = _draw_text_uniform(rng, n, alphabet)
+        k = int(rng.integers(k_min, k_max + 1))
+        pats = _draw_patterns(rng, k, lmin, lmax, alphabet=alphabet)
+        _plant(rng, text, pats, [int(round(density * n))] * k)
+        texts.append(text)
+        tables.append(pats)
+    return Batch("batched", texts, tables, list(range(n_items)),
+                 dict(seed=seed, n_items=n_items, min_len=min_len, max_len=max_len, k_min=k_min,
+                      k_max=k_max, lmin=lmin, lmax=lmax, density=density))
+
+
 #: Full-size configurations: the 1 MiB DNA search, the 1 GiB Zipf scan and the
 #: 4 GiB signature set.
 FULL = {
