@@ -249,6 +249,58 @@ int rk_batch_read(const rk_batch *b, uint64_t *h_keys, uint64_t key_cap, uint64_
 int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t reps, double *best_ms,
                       void *stream);
 
+/* ---- serving ---------------------------------------------------------------
+ * A request loop over a resident table set.  Requests (a host text and a
+ * table id) are admitted while their texts fit in a device-memory arena of
+ * mem_cap bytes, copied to the device, and packed into batched launches on
+ * `engines` batch engines; requests arriving while batches run are admitted
+ * and copied meanwhile and go into the next free engine.  Each request gets
+ * its own sorted match list in the single-text key format RK_KEY(id, x).   */
+typedef struct rk_server rk_server;
+
+typedef struct rk_server_opts {
+    uint64_t mem_cap;          /* device bytes for admitted texts (the admission cap) */
+    uint64_t max_text_len;     /* longest request text, <= mem_cap */
+    uint64_t max_batch_bytes;  /* most text bytes per batch (default mem_cap) */
+    uint64_t batch_capacity;   /* match keys per batch (default 2^22) */
+    uint32_t engines;          /* batches in flight, 1..8 (default 2) */
+    uint32_t max_batch_items;  /* requests per batch (default 1024) */
+    uint32_t tile_bytes, warps;  /* launch shape of the batch kernel (0 = default) */
+} rk_server_opts;
+
+typedef struct rk_request_times {
+    double arrive_us, admit_us, launch_us, done_us;  /* since the server started */
+} rk_request_times;
+
+typedef struct rk_server_stats {
+    uint64_t requests_done, bytes_done, batches, items_batched;
+    uint64_t waiting, in_flight, arena_used;
+    double now_us;
+} rk_server_stats;
+
+/* Start a server (and its worker thread) on the current device.  The table
+ * set must outlive it.  Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA.             */
+int rk_server_create(const rk_tableset *ts, const rk_server_opts *opts, rk_server **out);
+
+/* Finish every submitted request, stop the worker and free everything.     */
+void rk_server_destroy(rk_server *s);
+
+/* Submit a request: search h_text[0..n) (host memory, valid and unchanged
+ * until the request is taken) with table `table`.  *request_id identifies it.
+ * Errors: RK_EINVAL (table, length beyond max_text_len), RK_ENOMEM.         */
+int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_text, uint64_t n,
+                     uint64_t *request_id);
+
+/* Wait up to timeout_ms (< 0: forever) for a request and take its result:
+ * *n_keys gets the match count, h_keys[0..n_keys) the sorted keys, *times
+ * (may be NULL) its timestamps.  RK_ECAPACITY: key_cap < *n_keys, the result
+ * is kept (call again); RK_ETIMEOUT: not finished yet.  Other errors: the
+ * request failed and is released.                                           */
+int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms, uint64_t *h_keys,
+                   uint64_t key_cap, uint64_t *n_keys, rk_request_times *times);
+
+int rk_server_stats_get(rk_server *s, rk_server_stats *stats);
+
 /* ---- search without allocation ------------------------------------------
  * No counterpart in the paper: a convenience for callers that cannot allocate.
  *

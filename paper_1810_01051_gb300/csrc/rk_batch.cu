@@ -318,18 +318,6 @@ using namespace rk;
 
 // ---------------------------------------------------------------- table sets
 
-struct rk_tableset {
-    int device = 0, sm_count = 0;
-    uint32_t n_tables = 0;
-    void *d_mem = nullptr;
-    size_t d_bytes = 0;
-    const DevTable *d_tables = nullptr;  // device array
-    uint32_t filter_mode = kFilterFlat;
-    uint32_t max_filter_bytes = 0, max_s2_bytes = 0, max_lmax = 1, max_patterns = 0;
-    bool all_q4 = true;
-    std::vector<uint32_t> npat;  // patterns per table
-};
-
 extern "C" int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, const uint32_t *lens,
                                  const uint32_t *patterns_per_table, const rk_build_opts *opts,
                                  rk_tableset **out) {

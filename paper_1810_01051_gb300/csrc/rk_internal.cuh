@@ -116,6 +116,19 @@ struct rk_table {
     std::vector<cudaEvent_t> events;
 };
 
+// Host object behind a table-set handle: many tables in one allocation.
+struct rk_tableset {
+    int device = 0, sm_count = 0;
+    uint32_t n_tables = 0;
+    void *d_mem = nullptr;
+    size_t d_bytes = 0;
+    const rk::DevTable *d_tables = nullptr;  // device array
+    uint32_t filter_mode = rk::kFilterFlat;
+    uint32_t max_filter_bytes = 0, max_s2_bytes = 0, max_lmax = 1, max_patterns = 0;
+    bool all_q4 = true;
+    std::vector<uint32_t> npat;  // patterns per table
+};
+
 namespace rk {
 
 // Host image of one pattern table (all parts 256-byte aligned) and the

@@ -1,0 +1,441 @@
+// Serving loop: search requests arrive with host texts and a resident table
+// id; a worker thread admits them while their texts fit in a device-memory
+// arena (the admission cap), copies the texts on a copy stream, packs the
+// requests whose texts have landed into whichever batch engine is free (each
+// engine: an rk_batch with its own stream and captured graph), and hands each
+// request its sorted match list.  New requests are admitted and copied while
+// earlier batches run (continuous batching); a finished batch frees its
+// requests' memory for the next arrivals.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+
+#include "rk_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over one device arena (offsets, 256-byte granules).
+class Arena {
+  public:
+    void reset(uint64_t bytes) {
+        free_.clear();
+        free_[0] = bytes;
+        used_ = 0;
+    }
+    bool alloc(uint64_t n, uint64_t *off) {
+        n = (n + 255) / 256 * 256;
+        if (n == 0) n = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const uint64_t rest = it->second - n, at = it->first + n;
+            free_.erase(it);
+            if (rest) free_[at] = rest;
+            used_ += n;
+            sizes_[*off] = n;
+            return true;
+        }
+        return false;
+    }
+    void release(uint64_t off) {
+        auto s = sizes_.find(off);
+        if (s == sizes_.end()) return;
+        uint64_t n = s->second;
+        sizes_.erase(s);
+        used_ -= n;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+    uint64_t used() const { return used_; }
+
+  private:
+    std::map<uint64_t, uint64_t> free_;   // offset -> bytes
+    std::map<uint64_t, uint64_t> sizes_;  // allocated offset -> bytes
+    uint64_t used_ = 0;
+};
+
+struct Request {
+    uint64_t id = 0;
+    uint32_t table = 0;
+    const uint8_t *h_text = nullptr;
+    uint64_t n = 0;
+    uint64_t arena_off = 0;
+    bool on_arena = false;
+    cudaEvent_t copied = nullptr;
+    double t_arrive = 0, t_admit = 0, t_launch = 0, t_done = 0;
+    int status = RK_OK;
+    std::vector<uint64_t> keys;  // (id << 40) | x, ascending
+};
+
+struct Engine {
+    rk_batch *b = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<Request *> reqs;
+    uint64_t *h_keys = nullptr;     // pinned: the batch's sorted keys
+    uint64_t *h_offsets = nullptr;  // pinned: item offsets
+};
+
+}  // namespace
+
+struct rk_server {
+    const rk_tableset *ts = nullptr;
+    rk_server_opts opts{};
+    int device = 0;
+    uint8_t *arena_mem = nullptr;
+    Arena arena;
+    std::vector<Engine> engines;
+    cudaStream_t copy_stream = nullptr;
+    Clock::time_point t0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> arrived, copying, ready;
+    std::unordered_map<uint64_t, Request *> finished;
+    uint64_t next_id = 1;
+    uint32_t batch_limit = 0;  // items per batch after an overflow (0: no limit)
+    bool stop = false;
+    int fatal = RK_OK;
+    uint64_t bytes_done = 0, requests_done = 0, batches = 0, items_batched = 0;
+    std::vector<cudaEvent_t> spare_events;
+    std::thread worker;
+
+    double now_us() const {
+        return std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+cudaEvent_t take_event(rk_server *s) {
+    if (!s->spare_events.empty()) {
+        cudaEvent_t e = s->spare_events.back();
+        s->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+}
+
+void finish(rk_server *s, Request *r, int status) {
+    r->status = status;
+    r->t_done = s->now_us();
+    if (r->on_arena) s->arena.release(r->arena_off);
+    r->on_arena = false;
+    if (r->copied) s->spare_events.push_back(r->copied);
+    r->copied = nullptr;
+    s->finished[r->id] = r;
+    s->bytes_done += r->n;
+    s->requests_done += 1;
+}
+
+// Collect a finished engine's results into its requests (mutex held).  A
+// batch whose matches overflowed the key capacity goes back to the head of the
+// ready queue and later batches take half as many requests; a single request
+// that overflows alone fails with RK_ECAPACITY.
+void harvest(rk_server *s, Engine &e) {
+    uint64_t info[2] = {0, 0};
+    const uint32_t n_items = (uint32_t)e.reqs.size();
+    rk_batch_info bi{};
+    rk_batch_info_get(e.b, &bi);
+    const uint64_t *keys = e.h_keys, *offs = e.h_offsets;
+    int rc = rk_batch_read(e.b, e.h_keys, s->opts.batch_capacity, e.h_offsets, info, e.st);
+    if (rc == RK_OK && info[1] == RK_OK && info[0] > s->opts.batch_capacity && n_items > 1) {
+        for (uint32_t i = n_items; i-- > 0;) s->ready.push_front(e.reqs[i]);
+        s->batch_limit = std::max<uint32_t>(1, n_items / 2);
+        e.reqs.clear();
+        e.busy = false;
+        return;
+    }
+    const double t = s->now_us();
+    for (uint32_t i = 0; i < n_items; ++i) {
+        Request *r = e.reqs[i];
+        if (rc != RK_OK || info[1] != RK_OK) {
+            finish(s, r, rc != RK_OK ? rc : (int)info[1]);
+            continue;
+        }
+        if (info[0] > s->opts.batch_capacity) {
+            finish(s, r, RK_ECAPACITY);
+            continue;
+        }
+        const uint64_t lo = offs[i], hi = offs[i + 1];
+        const uint64_t omask = (1ull << bi.offset_bits) - 1;
+        const uint64_t imask = (1ull << bi.id_bits) - 1;
+        r->keys.resize(hi - lo);
+        for (uint64_t j = lo; j < hi; ++j) {
+            const uint64_t k = keys[j];
+            r->keys[j - lo] =
+                (((k >> bi.offset_bits) & imask) << RK_KEY_OFFSET_BITS) | (k & omask);
+        }
+        finish(s, r, RK_OK);
+        r->t_done = t;
+    }
+    s->batches += 1;
+    s->items_batched += n_items;
+    e.reqs.clear();
+    e.busy = false;
+}
+
+void loop(rk_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        bool progress = false;
+        // 1. admit arrivals while their texts fit in the arena
+        while (!s->arrived.empty()) {
+            Request *r = s->arrived.front();
+            uint64_t off = 0;
+            if (!s->arena.alloc(r->n, &off)) break;  // wait for memory to free up
+            s->arrived.pop_front();
+            r->arena_off = off;
+            r->on_arena = true;
+            r->t_admit = s->now_us();
+            r->copied = take_event(s);
+            if (r->n)
+                cudaMemcpyAsync(s->arena_mem + off, r->h_text, r->n, cudaMemcpyHostToDevice,
+                                s->copy_stream);
+            cudaEventRecord(r->copied, s->copy_stream);
+            s->copying.push_back(r);
+            progress = true;
+        }
+        // 2. texts that have landed become ready, in arrival order
+        while (!s->copying.empty() && cudaEventQuery(s->copying.front()->copied) == cudaSuccess) {
+            s->ready.push_back(s->copying.front());
+            s->copying.pop_front();
+            progress = true;
+        }
+        // 3. finished batches hand back results and memory
+        for (Engine &e : s->engines) {
+            if (e.busy && cudaEventQuery(e.done) == cudaSuccess) {
+                harvest(s, e);
+                progress = true;
+            }
+        }
+        if (progress) s->cv_done.notify_all();
+        // 4. pack ready requests into free engines
+        for (Engine &e : s->engines) {
+            if (e.busy || s->ready.empty()) continue;
+            std::vector<uint32_t> tabs;
+            std::vector<const uint8_t *> texts;
+            std::vector<uint64_t> lens;
+            uint64_t bytes = 0;
+            const uint32_t limit = s->batch_limit ? s->batch_limit : s->opts.max_batch_items;
+            while (!s->ready.empty() && e.reqs.size() < limit &&
+                   bytes + s->ready.front()->n <= s->opts.max_batch_bytes) {
+                Request *r = s->ready.front();
+                s->ready.pop_front();
+                bytes += r->n;
+                e.reqs.push_back(r);
+                tabs.push_back(r->table);
+                texts.push_back(s->arena_mem + r->arena_off);
+                lens.push_back(r->n);
+            }
+            if (e.reqs.empty()) continue;
+            const double t = s->now_us();
+            for (Request *r : e.reqs) r->t_launch = t;
+            int rc = rk_batch_set(e.b, (uint32_t)e.reqs.size(), tabs.data(), texts.data(),
+                                  lens.data(), e.st);
+            if (rc == RK_OK) rc = rk_batch_run(e.b, e.st);
+            if (rc == RK_OK && cudaEventRecord(e.done, e.st) != cudaSuccess) rc = RK_ECUDA;
+            if (rc != RK_OK) {
+                for (Request *r : e.reqs) finish(s, r, rc);
+                e.reqs.clear();
+                s->cv_done.notify_all();
+                continue;
+            }
+            e.busy = true;
+            progress = true;
+        }
+        bool idle = true;
+        for (Engine &e : s->engines) idle = idle && !e.busy;
+        if (s->stop && s->arrived.empty() && s->copying.empty() && s->ready.empty() && idle) break;
+        if (!progress) {
+            // nothing changed: wait for a submit, or poll the GPU again shortly
+            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int rk_server_create(const rk_tableset *ts, const rk_server_opts *opts,
+                                rk_server **out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    if (!ts || !opts) return RK_EINVAL;
+    rk_server_opts o = *opts;
+    if (!o.engines) o.engines = 2;
+    if (!o.max_batch_items) o.max_batch_items = 1024;
+    if (!o.max_text_len || !o.mem_cap) return RK_EINVAL;
+    if (!o.max_batch_bytes) o.max_batch_bytes = o.mem_cap;
+    if (!o.batch_capacity) o.batch_capacity = 1 << 22;
+    if (o.engines > 8 || o.max_text_len > o.mem_cap) return RK_EINVAL;
+    rk_server *s = new (std::nothrow) rk_server();
+    if (!s) return RK_ENOMEM;
+    s->ts = ts;
+    s->opts = o;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return RK_ECUDA;
+    }
+    if (cudaMalloc(&s->arena_mem, o.mem_cap) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return RK_ENOMEM;
+    }
+    s->arena.reset(o.mem_cap);
+    int rc = RK_OK;
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = RK_ECUDA;
+    s->engines.resize(o.engines);
+    for (Engine &e : s->engines) {
+        if (rc) break;
+        rk_batch_opts bo{};
+        bo.max_items = o.max_batch_items;
+        bo.max_text_len = o.max_text_len;
+        bo.max_total_bytes = o.max_batch_bytes;
+        bo.capacity = o.batch_capacity;
+        bo.tile_bytes = o.tile_bytes;
+        bo.warps = o.warps;
+        rc = rk_batch_create(ts, &bo, &e.b);
+        if (!rc && (cudaStreamCreateWithFlags(&e.st, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess))
+            rc = RK_ECUDA;
+        if (!rc && (cudaMallocHost(&e.h_keys, 8 * o.batch_capacity) != cudaSuccess ||
+                    cudaMallocHost(&e.h_offsets, 8ull * (o.max_batch_items + 1)) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = RK_ENOMEM;
+        }
+    }
+    if (rc) {
+        rk_server_destroy(s);
+        return rc;
+    }
+    s->t0 = Clock::now();
+    s->worker = std::thread(loop, s);
+    *out = s;
+    return RK_OK;
+}
+
+extern "C" void rk_server_destroy(rk_server *s) {
+    if (!s) return;
+    if (s->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        s->worker.join();
+    }
+    for (Engine &e : s->engines) {
+        if (e.st) cudaStreamSynchronize(e.st);
+        rk_batch_destroy(e.b);
+        if (e.st) cudaStreamDestroy(e.st);
+        if (e.done) cudaEventDestroy(e.done);
+        if (e.h_keys) cudaFreeHost(e.h_keys);
+        if (e.h_offsets) cudaFreeHost(e.h_offsets);
+    }
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
+    }
+    for (auto &kv : s->finished) {
+        if (kv.second->copied) cudaEventDestroy(kv.second->copied);
+        delete kv.second;
+    }
+    for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    cudaFree(s->arena_mem);
+    delete s;
+}
+
+extern "C" int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_text, uint64_t n,
+                                uint64_t *request_id) {
+    if (!s || !request_id || (n && !h_text)) return RK_EINVAL;
+    if (table >= s->ts->n_tables || n > s->opts.max_text_len || n > s->opts.max_batch_bytes)
+        return RK_EINVAL;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return RK_ENOMEM;
+    r->table = table;
+    r->h_text = h_text;
+    r->n = n;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete r;
+            return RK_EINVAL;
+        }
+        r->id = s->next_id++;
+        r->t_arrive = s->now_us();
+        s->arrived.push_back(r);
+        *request_id = r->id;
+    }
+    s->cv_work.notify_one();
+    return RK_OK;
+}
+
+extern "C" int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms, uint64_t *h_keys,
+                              uint64_t key_cap, uint64_t *n_keys, rk_request_times *times) {
+    if (!s || !n_keys) return RK_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto pred = [&] { return s->finished.count(request_id) != 0; };
+    if (timeout_ms < 0) s->cv_done.wait(lk, pred);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return RK_ETIMEOUT;
+    Request *r = s->finished[request_id];
+    *n_keys = r->keys.size();
+    if (times) {
+        times->arrive_us = r->t_arrive;
+        times->admit_us = r->t_admit;
+        times->launch_us = r->t_launch;
+        times->done_us = r->t_done;
+    }
+    if (r->status != RK_OK) {
+        const int st = r->status;
+        s->finished.erase(request_id);
+        delete r;
+        return st;
+    }
+    if (r->keys.size() > key_cap) return RK_ECAPACITY;  // kept: call again with a larger buffer
+    if (h_keys && !r->keys.empty()) std::copy(r->keys.begin(), r->keys.end(), h_keys);
+    s->finished.erase(request_id);
+    delete r;
+    return RK_OK;
+}
+
+extern "C" int rk_server_stats_get(rk_server *s, rk_server_stats *st) {
+    if (!s || !st) return RK_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    rk_server_stats r{};
+    r.requests_done = s->requests_done;
+    r.bytes_done = s->bytes_done;
+    r.batches = s->batches;
+    r.items_batched = s->items_batched;
+    r.waiting = s->arrived.size();
+    r.in_flight = s->copying.size() + s->ready.size();
+    for (const Engine &e : s->engines) r.in_flight += e.reqs.size();
+    r.arena_used = s->arena.used();
+    r.now_us = s->now_us();
+    *st = r;
+    return RK_OK;
+}

@@ -32,7 +32,8 @@ EXPORTS = [
     "rk_window_hashes_device", "rk_search_device_noalloc",
     "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
     "rk_batch_info_get", "rk_batch_set", "rk_batch_run", "rk_batch_results", "rk_batch_read",
-    "rk_batch_autotune",
+    "rk_batch_autotune", "rk_server_create", "rk_server_destroy", "rk_server_submit",
+    "rk_server_take", "rk_server_stats_get",
 ]
 
 
@@ -66,6 +67,22 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "offset_bits", "id_bits", "item_bits", "warps", "tile_bytes", "stages", "ctas_per_sm",
         "s2_in_smem", "smem_bytes", "n_chunks", "max_chunks")]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "mem_cap", "max_text_len", "max_batch_bytes", "batch_capacity")] + [
+        (n, ctypes.c_uint32) for n in ("engines", "max_batch_items", "tile_bytes", "warps")]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("arrive_us", "admit_us", "launch_us", "done_us")]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "requests_done", "bytes_done", "batches", "items_batched", "waiting", "in_flight",
+        "arena_used")] + [("now_us", ctypes.c_double)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -128,6 +145,17 @@ def load() -> ctypes.CDLL:
     L.rk_batch_read.argtypes = [vp, vp, u64, vp, vp, vp]
     L.rk_batch_autotune.restype = ctypes.c_int
     L.rk_batch_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_double), vp]
+    L.rk_server_create.restype = ctypes.c_int
+    L.rk_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    L.rk_server_destroy.restype = None
+    L.rk_server_destroy.argtypes = [vp]
+    L.rk_server_submit.restype = ctypes.c_int
+    L.rk_server_submit.argtypes = [vp, u32, vp, u64, ctypes.POINTER(u64)]
+    L.rk_server_take.restype = ctypes.c_int
+    L.rk_server_take.argtypes = [vp, u64, ctypes.c_int, vp, u64, ctypes.POINTER(u64),
+                                 ctypes.POINTER(RequestTimes)]
+    L.rk_server_stats_get.restype = ctypes.c_int
+    L.rk_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
     _lib = L
     return L
 
@@ -317,6 +345,51 @@ def rk_batch_autotune(b: int, max_candidates: int = 0, reps: int = 3, stream=Non
     _check(load().rk_batch_autotune(b, max_candidates, reps, ctypes.byref(best), _stream(stream)),
            "rk_batch_autotune")
     return best.value
+
+
+def rk_server_create(ts: int, mem_cap: int, max_text_len: int, max_batch_bytes: int = 0,
+                     batch_capacity: int = 0, engines: int = 0, max_batch_items: int = 0,
+                     tile_bytes: int = 0, warps: int = 0) -> int:
+    opts = ServerOpts(mem_cap, max_text_len, max_batch_bytes, batch_capacity, engines,
+                      max_batch_items, tile_bytes, warps)
+    out = ctypes.c_void_p()
+    _check(load().rk_server_create(ts, ctypes.byref(opts), ctypes.byref(out)), "rk_server_create")
+    return int(out.value)
+
+
+def rk_server_destroy(s: int) -> None:
+    load().rk_server_destroy(s)
+
+
+def rk_server_submit(s: int, table: int, h_text, n: int) -> int:
+    """The host buffer must stay alive and unchanged until the request is taken."""
+    rid = ctypes.c_uint64(0)
+    _check(load().rk_server_submit(s, table, _ptr(h_text) if n else None, n, ctypes.byref(rid)),
+           "rk_server_submit")
+    return int(rid.value)
+
+
+def rk_server_take(s: int, request_id: int, timeout_ms: int = -1, key_cap: int = 1 << 16):
+    """(status, keys uint64[], times dict); grows the buffer when it is too small.
+    status RK_ETIMEOUT: not finished within timeout_ms."""
+    L = load()
+    while True:
+        keys = np.empty(max(key_cap, 1), dtype=np.uint64)
+        n = ctypes.c_uint64(0)
+        t = RequestTimes()
+        rc = L.rk_server_take(s, request_id, timeout_ms, keys.ctypes.data, key_cap,
+                              ctypes.byref(n), ctypes.byref(t))
+        if rc == RK_ECAPACITY and n.value > key_cap:
+            key_cap = int(n.value)
+            continue
+        times = {name: getattr(t, name) for name, _ in RequestTimes._fields_}
+        return rc, keys[:n.value].copy() if rc == RK_OK else keys[:0], times
+
+
+def rk_server_stats(s: int) -> dict:
+    st = ServerStats()
+    _check(load().rk_server_stats_get(s, ctypes.byref(st)), "rk_server_stats_get")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
 
 
 def unpack_batch_keys(keys: np.ndarray, offset_bits: int, id_bits: int):

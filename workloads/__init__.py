@@ -14,4 +14,6 @@ from .gen import (  # noqa: F401
     make_config,
     Batch,
     batched,
+    serving_tables,
+    serving_texts,
 )

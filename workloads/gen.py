@@ -226,6 +226,34 @@ def batched(seed: int = 0x5EED0003, n_items: int = 4096, min_len: int = 1 << 10,
                       k_max=k_max, lmin=lmin, lmax=lmax, density=density))
 
 
+def serving_tables(seed: int = 0x5EED0004, n_tables: int = 64, k_max: int = 1024, lmin: int = 4,
+                   lmax: int = 64) -> List[List[bytes]]:
+    """Resident tables of the serving workload: table j holds U{1..k_max}
+    uniform-byte patterns of lengths U{lmin..lmax}."""
+    rng = np.random.default_rng(seed)
+    tables = []
+    for _ in range(n_tables):
+        k = int(rng.integers(1, k_max + 1))
+        tables.append(_draw_patterns(rng, k, lmin, lmax))
+    return tables
+
+
+def serving_texts(seed: int, n: int, tables: List[List[bytes]], min_len: int = 4 << 10,
+                  max_len: int = 64 << 20, density: float = 1e-5):
+    """n requests: (table id, text) with a uniform table choice, a log-uniform
+    text length in [min_len, max_len] of uniform bytes, and every pattern of
+    the table planted round(density * len) times."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        tid = int(rng.integers(0, len(tables)))
+        L = int(np.exp(rng.uniform(np.log(min_len), np.log(max_len))))
+        text = _draw_text_uniform(rng, L, None)
+        _plant(rng, text, tables[tid], [int(round(density * L))] * len(tables[tid]))
+        out.append((tid, text))
+    return out
+
+
 #: Full-size configurations: the 1 MiB DNA search, the 1 GiB Zipf scan and the
 #: 4 GiB signature set.
 FULL = {
