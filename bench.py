@@ -180,6 +180,182 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------- batched and served
+
+def measure_batched(torch, rk, dev, max_len, reps=5, tune_candidates=12):
+    """Batched workload (4096 texts, log-uniform lengths up to max_len, 20
+    letters, 1..256 patterns of 4..48 bytes per text): one autotuned graph
+    replay for all texts against one plain launch (scan + sort) per text."""
+    from workloads import batched
+    bt = batched(n_items=4096, max_len=max_len)
+    n_items, total = len(bt.texts), bt.total_bytes
+    offs, at = [], 0
+    for t in bt.texts:
+        offs.append(at)
+        at += (t.size + 255) // 256 * 256
+    host = torch.empty(at + 256, dtype=torch.uint8, pin_memory=True)
+    hv = host.numpy()
+    for t, o in zip(bt.texts, offs):
+        hv[o:o + t.size] = t
+    d_all = host.to(dev)
+    ptrs = [d_all.data_ptr() + o for o in offs]
+    lens = [t.size for t in bt.texts]
+    st = torch.cuda.Stream(dev)
+    ts = rk.rk_tableset_build(bt.tables)
+    cap = 1 << 24
+    b = rk.rk_batch_create(ts, n_items, max(lens), total, cap)
+    try:
+        rk.rk_batch_set(b, bt.table_of, ptrs, lens, st)
+        tuned_ms = rk.rk_batch_autotune(b, max_candidates=tune_candidates, reps=2, stream=st)
+        info = rk.rk_batch_info(b)
+        rk.rk_batch_run(b, st)
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            rk.rk_batch_run(b, st)
+        e1.record(st)
+        st.synchronize()
+        batch_ms = e0.elapsed_time(e1) / reps
+        count, status, _, _ = rk.rk_batch_read(b, n_items, 0, st)
+    finally:
+        rk.rk_batch_destroy(b)
+        rk.rk_tableset_destroy(ts)
+    # plain per-request launches: one table and one search (scan + sort) per text
+    tabs = [rk.rk_build(p) for p in bt.tables]
+    try:
+        pcap = 1 << 20
+        keys = torch.empty(pcap, dtype=torch.int64, device=dev)
+        infos = torch.zeros(n_items, 2, dtype=torch.int64, device=dev)
+        wsb = rk.rk_workspace_bytes(tabs[0], pcap)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        for i in range(min(8, n_items)):  # warm-up
+            rk.rk_search_device(tabs[i], ptrs[i], lens[i], keys, pcap, infos[i], ws, wsb, st)
+        st.synchronize()
+        e0.record(st)
+        for i in range(n_items):
+            rk.rk_search_device(tabs[i], ptrs[i], lens[i], keys, pcap, infos[i], ws, wsb, st)
+        e1.record(st)
+        st.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        plain_count = int(infos[:, 0].sum().item())
+    finally:
+        for t in tabs:
+            rk.rk_destroy(t)
+    del d_all
+    return {
+        "workload": f"4096 texts, log-uniform 1 KiB..{max_len >> 20} MiB, 20 letters, "
+                    "1..256 patterns of 4..48 bytes each, density 1e-5",
+        "text_bytes": total, "matches": count, "status": status,
+        "matches_equal_per_request": count == plain_count,
+        "batched_gbps": total / (batch_ms / 1e3) / 1e9, "batched_ms": batch_ms,
+        "per_request_gbps": total / (plain_ms / 1e3) / 1e9, "per_request_ms": plain_ms,
+        "speedup": plain_ms / batch_ms, "autotuned_scan_ms": tuned_ms,
+        "tuned": {k: info[k] for k in ("warps", "tile_bytes", "stages", "ctas_per_sm",
+                                       "s2_in_smem")},
+    }
+
+
+def measure_serving(torch, rk, dev, n_req=200, loads=(0.5, 1.0, 2.0, 4.0, 8.0), pool_size=48):
+    """Serving workload (64 resident tables of 1..1024 patterns of 4..64 bytes;
+    requests of log-uniform 4 KiB..64 MiB uniform bytes, Poisson arrivals):
+    p50/p99 latency and GB/s at offered loads relative to the plain
+    per-request call's throughput, for the server and for plain calls."""
+    import random
+    from workloads import serving_tables, serving_texts
+    tables = serving_tables()
+    pool = serving_texts(0x5EED0005, pool_size, tables)
+    pinned = []
+    for tid, text in pool:
+        h = torch.empty(text.size, dtype=torch.uint8, pin_memory=True)
+        h.numpy()[:] = text
+        pinned.append((tid, h))
+    mean_bytes = sum(h.numel() for _, h in pinned) / len(pinned)
+    tabs = [rk.rk_build(t) for t in tables]
+    hkeys = torch.empty(1 << 20, dtype=torch.int64, pin_memory=True)
+
+    def plain(tid, h):
+        rc, cnt = rk.rk_search(tabs[tid], h, h.numel(), hkeys, hkeys.numel())
+        return cnt
+
+    try:
+        for tid, h in pinned[:4]:
+            plain(tid, h)
+        t0 = time.perf_counter()
+        for tid, h in pinned:
+            plain(tid, h)
+        plain_gbps = sum(h.numel() for _, h in pinned) / (time.perf_counter() - t0) / 1e9
+        ts = rk.rk_tableset_build(tables)
+        free, _ = torch.cuda.mem_get_info(dev)
+        cap = int(min(64 << 30, free // 4))
+        srv = rk.rk_server_create(ts, mem_cap=cap, max_text_len=64 << 20,
+                                  batch_capacity=1 << 23, engines=2, max_batch_items=256)
+        rng = random.Random(7)
+        levels = []
+        try:
+            for tid, h in pinned[:16]:  # warm-up: engines, events, arena
+                rk.rk_server_take(srv, rk.rk_server_submit(srv, tid, h, h.numel()),
+                                  timeout_ms=120000, key_cap=1 << 22)
+            for load in loads:
+                rate = load * plain_gbps * 1e9 / mean_bytes  # requests per second
+                arrivals, t = [], 0.0
+                for _ in range(n_req):
+                    t += rng.expovariate(rate)
+                    arrivals.append(t)
+                picks = [rng.randrange(len(pinned)) for _ in range(n_req)]
+                # served: submit at the arrival times, then collect
+                start = time.perf_counter()
+                ids = []
+                for at, i in zip(arrivals, picks):
+                    while time.perf_counter() - start < at:
+                        pass
+                    tid, h = pinned[i]
+                    ids.append(rk.rk_server_submit(srv, tid, h, h.numel()))
+                lat, first, last = [], None, 0.0
+                for rid in ids:
+                    rc, _, tm = rk.rk_server_take(srv, rid, timeout_ms=120000, key_cap=1 << 22)
+                    lat.append(tm["done_us"] - tm["arrive_us"])
+                    first = tm["arrive_us"] if first is None else min(first, tm["arrive_us"])
+                    last = max(last, tm["done_us"])
+                nbytes = sum(pinned[i][1].numel() for i in picks)
+                # plain per-request calls, one at a time in arrival order
+                start = time.perf_counter()
+                plat, busy_until = [], 0.0
+                for at, i in zip(arrivals, picks):
+                    now = time.perf_counter() - start
+                    if now < at:
+                        while time.perf_counter() - start < at:
+                            pass
+                    tid, h = pinned[i]
+                    plain(tid, h)
+                    plat.append((time.perf_counter() - start - at) * 1e6)
+                plain_span = time.perf_counter() - start - arrivals[0]
+                levels.append({
+                    "offered_load": load, "offered_gbps": load * plain_gbps,
+                    "served_gbps": nbytes / ((last - first) / 1e6) / 1e9,
+                    "served_p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                    "served_p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                    "plain_gbps": nbytes / plain_span / 1e9,
+                    "plain_p50_ms": float(np.percentile(plat, 50)) / 1e3,
+                    "plain_p99_ms": float(np.percentile(plat, 99)) / 1e3,
+                })
+            stats = rk.rk_server_stats(srv)
+        finally:
+            rk.rk_server_destroy(srv)
+            rk.rk_tableset_destroy(ts)
+    finally:
+        for t in tabs:
+            rk.rk_destroy(t)
+    return {
+        "workload": "64 resident tables (1..1024 patterns, 4..64 bytes), requests log-uniform "
+                    "4 KiB..64 MiB uniform bytes, Poisson arrivals, host texts in pinned memory",
+        "requests_per_level": n_req, "mean_request_bytes": mean_bytes,
+        "plain_closed_loop_gbps": plain_gbps, "admission_cap_bytes": cap,
+        "batches": stats["batches"], "items_batched": stats["items_batched"],
+        "levels": levels,
+    }
+
+
 # ---------------------------------------------------------------- our arm
 
 def sort_launches(n, k):
@@ -293,6 +469,15 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     clocks = sampler.stop()
 
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        for name, fn in (("batched", lambda: measure_batched(torch, rk, dev, 2 << 20)),
+                         ("served", lambda: measure_serving(torch, rk, dev))):
+            try:
+                extra[name] = fn()
+            except Exception as exc:  # a failed extra must not lose the main line
+                extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
     if world > 1:
         t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -351,6 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -366,6 +552,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served comparisons")
+    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
+                    help="batched: the full 4096-text batch (up to 16 MiB per text) alone")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -374,7 +564,26 @@ def main():
     local_rank = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched_full(args)
     return run_ours(args, rank, world, local_rank)
+
+
+def run_batched_full(args):
+    import torch
+    from paper_1810_01051_gb300 import build_lib, rk
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = measure_batched(torch, rk, dev, 16 << 20, reps=max(3, min(args.steps, 20)))
+    line = {"metric": METRIC + " [batched workload]", "value": r["batched_gbps"], "unit": UNIT,
+            "n_gpus": 1, "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
+            "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": r["workload"], "text_bytes": r["text_bytes"]},
+            "batched": r}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -171,8 +171,19 @@ cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint3
                      cudaStream_t st) {
     auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true>
                         : rk_scan_tiles_kernel<MODE, Q4, MAXW, false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // raise the dynamic shared-memory limit once per device and size
+    static thread_local int seen_dev[4] = {-1, -1, -1, -1};
+    static thread_local uint32_t seen_smem[4] = {0, 0, 0, 0};
+    const int slot = p.s2_smem ? 1 : 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (seen_dev[slot] != dev || seen_smem[slot] < smem) {
+        cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        seen_dev[slot] = dev;
+        seen_smem[slot] = smem;
+    }
     fn<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
