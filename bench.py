@@ -356,6 +356,58 @@ def measure_serving(torch, rk, dev, n_req=200, loads=(0.5, 1.0, 2.0, 4.0, 8.0), 
     }
 
 
+def measure_paper_kernel(torch, rk, dev, reps=5):
+    """The paper's workloads on this GPU: its own kernel (one thread per
+    offset, O(m) shift-add hash) against the tiled scan, for one pattern on
+    DNA-like text: 320 MB with m = 7 over the block sizes of Table 1, and
+    Table 3's pattern lengths on 2 MB."""
+    from workloads import dna_single
+    st = torch.cuda.Stream(dev)
+
+    def timed(fn):
+        fn()
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        st.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def ours(table, d, n):
+        cap = 1 << 16
+        keys = torch.empty(cap, dtype=torch.int64, device=dev)
+        info = torch.zeros(2, dtype=torch.int64, device=dev)
+        wsb = rk.rk_workspace_bytes(table, cap)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        return lambda: rk.rk_search_device(table, d, n, keys, cap, info, ws, wsb, st)
+
+    out = {"table1_dna_320MB_m7": {}, "table3_dna_2MB": {}}
+    w = dna_single(seed=0x5EED0101, n=320_000_000, k=1, m=7, plants=100)
+    d = torch.from_numpy(w.text).to(dev)
+    res = torch.empty(w.n, dtype=torch.uint8, device=dev)
+    for tpb in (32, 64, 128, 256, 512, 1024):
+        ms = timed(lambda: rk.rk_paper_search_device(d, w.n, w.patterns[0], res, tpb, st))
+        out["table1_dna_320MB_m7"][f"paper_kernel_tpb{tpb}_ms"] = ms
+    t = rk.rk_build(w.patterns)
+    out["table1_dna_320MB_m7"]["tiled_scan_ms"] = timed(ours(t, d, w.n))
+    rk.rk_destroy(t)
+    del d, res
+    for m in (25, 50, 100, 200, 800):
+        w = dna_single(seed=0x5EED0200 + m, n=2_000_000, k=1, m=m, plants=20)
+        d = torch.from_numpy(w.text).to(dev)
+        res = torch.empty(w.n, dtype=torch.uint8, device=dev)
+        pk = timed(lambda: rk.rk_paper_search_device(d, w.n, w.patterns[0], res, 1024, st))
+        t = rk.rk_build(w.patterns)
+        ok = timed(ours(t, d, w.n))
+        rk.rk_destroy(t)
+        out["table3_dna_2MB"][f"m{m}"] = {"paper_kernel_ms": pk, "tiled_scan_ms": ok}
+    out["note"] = ("times on this GB300; the paper's Table 1 reports 847.1 ms (1024 threads per "
+                   "block, GeForce 920) and Table 3 7.5..201.2 ms for m = 25..800")
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def sort_launches(n, k):
@@ -472,7 +524,8 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: measure_batched(torch, rk, dev, 2 << 20)),
-                         ("served", lambda: measure_serving(torch, rk, dev))):
+                         ("served", lambda: measure_serving(torch, rk, dev)),
+                         ("paper_kernel", lambda: measure_paper_kernel(torch, rk, dev))):
             try:
                 extra[name] = fn()
             except Exception as exc:  # a failed extra must not lose the main line

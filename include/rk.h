@@ -167,6 +167,18 @@ int rk_search(const rk_table *t, const uint8_t *h_text, uint64_t n, uint64_t *h_
 int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint32_t base_log2,
                             uint64_t *d_hashes, void *stream);
 
+/* The paper's own GPU matcher (Section 3.1, GPU listing), kept as a measured
+ * comparison point: one pattern h_pattern[0..m) (host memory); one thread per
+ * text offset x = 0 .. n-m; the shift-add hash hy = (hy << 1) + T[x+i]
+ * recomputed over each window from global memory (64-bit, wrapping); a byte
+ * comparison when hy equals the pattern's hash, computed on the host; then
+ * d_result[x] = 1.  d_result: n bytes of device memory, zeroed by the call
+ * (1 = a match starts at x).  threads_per_block: multiple of 32, <= 1024
+ * (0: 1024), the paper's Table 1 parameter.  Asynchronous on `stream`.
+ * Errors: RK_EINVAL, RK_ECUDA.                                               */
+int rk_paper_search_device(const uint8_t *d_text, uint64_t n, const uint8_t *h_pattern, uint32_t m,
+                           uint8_t *d_result, uint32_t threads_per_block, void *stream);
+
 /* ---- batched search --------------------------------------------------------
  * Many texts, each searched with its own pattern table, in one launch: the
  * persistent batched kernel with its sort captured in a CUDA graph.

@@ -33,7 +33,7 @@ EXPORTS = [
     "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
     "rk_batch_info_get", "rk_batch_set", "rk_batch_run", "rk_batch_results", "rk_batch_read",
     "rk_batch_autotune", "rk_server_create", "rk_server_destroy", "rk_server_submit",
-    "rk_server_take", "rk_server_stats_get",
+    "rk_server_take", "rk_server_stats_get", "rk_paper_search_device",
 ]
 
 
@@ -156,6 +156,8 @@ def load() -> ctypes.CDLL:
                                  ctypes.POINTER(RequestTimes)]
     L.rk_server_stats_get.restype = ctypes.c_int
     L.rk_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.rk_paper_search_device.restype = ctypes.c_int
+    L.rk_paper_search_device.argtypes = [vp, u64, vp, u32, vp, u32, vp]
     _lib = L
     return L
 
@@ -265,6 +267,17 @@ def rk_search_device_noalloc(table: int, d_text, n: int, d_keys, capacity: int, 
     _check(load().rk_search_device_noalloc(table, _ptr(d_text), n, _ptr(d_keys), capacity,
                                            _ptr(d_info), _stream(stream)),
            "rk_search_device_noalloc")
+
+
+def rk_paper_search_device(d_text, n: int, pattern: bytes, d_result, threads_per_block: int = 0,
+                           stream=None) -> None:
+    """The paper's one-thread-per-offset matcher for one pattern; d_result[x] = 1
+    where a match starts."""
+    pat = np.frombuffer(bytes(pattern), dtype=np.uint8).copy()
+    _check(load().rk_paper_search_device(_ptr(d_text) if n else None, n, pat.ctypes.data,
+                                         len(pattern), _ptr(d_result) if n else None,
+                                         threads_per_block, _stream(stream)),
+           "rk_paper_search_device")
 
 
 # ------------------------------------------------------------------ batches
