@@ -179,6 +179,13 @@ int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint3
 int rk_paper_search_device(const uint8_t *d_text, uint64_t n, const uint8_t *h_pattern, uint32_t m,
                            uint8_t *d_result, uint32_t threads_per_block, void *stream);
 
+/* Diagnostics for failure detection: rk_scan_device with the producer
+ * issuing no copy, so every pipeline wait runs out after timeout_ms
+ * (1..10000).  The kernel then writes RK_ETIMEOUT to d_info[1] and returns;
+ * nothing faults and the context stays usable.  Errors: RK_EINVAL, RK_ECUDA. */
+int rk_debug_scan_withheld(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
+                           uint64_t capacity, uint64_t *d_info, uint32_t timeout_ms, void *stream);
+
 /* ---- batched search --------------------------------------------------------
  * Many texts, each searched with its own pattern table, in one launch: the
  * persistent batched kernel with its sort captured in a CUDA graph.

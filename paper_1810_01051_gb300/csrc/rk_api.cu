@@ -197,3 +197,15 @@ extern "C" int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32
                                                                      d_hashes);
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
+
+extern "C" int rk_debug_scan_withheld(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                                      uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                                      uint32_t timeout_ms, void *stream) {
+    int rc = scan_args_ok(t, d_text, n, d_keys, capacity, d_info);
+    if (rc) return rc;
+    if (timeout_ms == 0 || timeout_ms > 10000) return RK_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_info, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return RK_ECUDA;
+    return launch_scan_opts(t, d_text, n, 0, n, d_keys, capacity, d_info, st,
+                            (uint64_t)timeout_ms * 1000000ull, true);
+}

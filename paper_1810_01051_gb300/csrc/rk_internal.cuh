@@ -151,6 +151,12 @@ int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x
                 uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
                 cudaStream_t stream);
 
+// launch_scan with an explicit wait limit; `withhold` makes the producer
+// issue no copy (diagnostics: every consumer wait then runs out).
+int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
+                     uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                     cudaStream_t stream, uint64_t timeout_ns, bool withhold);
+
 int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);
 

@@ -36,7 +36,7 @@
 namespace rk {
 namespace {
 
-constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s per wait
+constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s per wait (default)
 
 struct ScanParams {
     DevTable tab;
@@ -50,7 +50,9 @@ struct ScanParams {
     uint64_t *keys;
     uint64_t capacity;
     unsigned long long *info;
+    uint64_t timeout_ns;     // limit of every pipeline wait
     uint32_t tile, stages, halo, warps, s2_smem;
+    uint32_t withhold;       // diagnostics: the producer issues no copy at all
 };
 
 // MAXW: most consumer warps this instance is launched with; the register
@@ -101,12 +103,12 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         P.n_tiles > blockIdx.x ? (P.n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (warp == nw) {  // ---------------- producer warp
-        if (lane != 0) return;
+        if (lane != 0 || P.withhold) return;
         uint64_t issued = 0;
         for (uint64_t i = 0; i < my_tiles; ++i) {
             const uint32_t s = (uint32_t)(i % P.stages);
             if (i >= P.stages &&
-                !mbar_wait_bounded(&empty[s], (uint32_t)((i / P.stages) + 1) & 1u, kWaitTimeoutNs)) {
+                !mbar_wait_bounded(&empty[s], (uint32_t)((i / P.stages) + 1) & 1u, P.timeout_ns)) {
                 s_abort = 1;
                 P.info[1] = RK_ETIMEOUT;
                 break;
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         }
         // every copy issued must have landed before the CTA may exit
         for (uint64_t i = issued > P.stages ? issued - P.stages : 0; i < issued; ++i)
-            mbar_wait_bounded(&full[i % P.stages], (uint32_t)(i / P.stages) & 1u, kWaitTimeoutNs);
+            mbar_wait_bounded(&full[i % P.stages], (uint32_t)(i / P.stages) & 1u, P.timeout_ns);
         return;
     }
 
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
 
     for (uint64_t i = 0; i < my_tiles; ++i) {
         const uint32_t s = (uint32_t)(i % P.stages);
-        if (!mbar_wait_bounded(&full[s], (uint32_t)(i / P.stages) & 1u, kWaitTimeoutNs)) {
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(i / P.stages) & 1u, P.timeout_ns)) {
             s_abort = 1;
             P.info[1] = RK_ETIMEOUT;
             break;
@@ -201,6 +203,13 @@ cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uin
 int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
                 uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
                 cudaStream_t stream) {
+    return launch_scan_opts(t, d_text, n, x_begin, x_end, d_keys, capacity, d_info, stream,
+                            kWaitTimeoutNs, false);
+}
+
+int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
+                     uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                     cudaStream_t stream, uint64_t timeout_ns, bool withhold) {
     if (x_end > n) x_end = n;
     if (x_begin >= x_end || t->dev.n_patterns == 0) return RK_OK;
     const Tuning &tu = t->tune;
@@ -223,6 +232,8 @@ int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x
     p.halo = tu.halo;
     p.warps = tu.warps;
     p.s2_smem = tu.s2_smem;
+    p.timeout_ns = timeout_ns;
+    p.withhold = withhold ? 1u : 0u;
     uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
     uint32_t grid = (uint32_t)(p.n_tiles < max_ctas ? p.n_tiles : max_ctas);
     uint32_t threads = (tu.warps + 1) * 32;

@@ -34,6 +34,7 @@ EXPORTS = [
     "rk_batch_info_get", "rk_batch_set", "rk_batch_run", "rk_batch_results", "rk_batch_read",
     "rk_batch_autotune", "rk_server_create", "rk_server_destroy", "rk_server_submit",
     "rk_server_take", "rk_server_stats_get", "rk_paper_search_device",
+    "rk_debug_scan_withheld",
 ]
 
 
@@ -158,6 +159,8 @@ def load() -> ctypes.CDLL:
     L.rk_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.rk_paper_search_device.restype = ctypes.c_int
     L.rk_paper_search_device.argtypes = [vp, u64, vp, u32, vp, u32, vp]
+    L.rk_debug_scan_withheld.restype = ctypes.c_int
+    L.rk_debug_scan_withheld.argtypes = [vp, vp, u64, vp, u64, vp, u32, vp]
     _lib = L
     return L
 
@@ -267,6 +270,15 @@ def rk_search_device_noalloc(table: int, d_text, n: int, d_keys, capacity: int, 
     _check(load().rk_search_device_noalloc(table, _ptr(d_text), n, _ptr(d_keys), capacity,
                                            _ptr(d_info), _stream(stream)),
            "rk_search_device_noalloc")
+
+
+def rk_debug_scan_withheld(table: int, d_text, n: int, d_keys, capacity: int, d_info,
+                           timeout_ms: int, stream=None) -> None:
+    """Failure-detection diagnostics: a scan whose copies never arrive, so its
+    bounded waits run out and d_info[1] becomes RK_ETIMEOUT."""
+    _check(load().rk_debug_scan_withheld(table, _ptr(d_text), n, _ptr(d_keys), capacity,
+                                         _ptr(d_info), timeout_ms, _stream(stream)),
+           "rk_debug_scan_withheld")
 
 
 def rk_paper_search_device(d_text, n: int, pattern: bytes, d_result, threads_per_block: int = 0,

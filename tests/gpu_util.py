@@ -25,7 +25,7 @@ def to_device(text: np.ndarray, misalign: int = 0) -> "torch.Tensor":
     buf = torch.zeros(n + misalign + 64, dtype=torch.uint8, device="cuda")
     view = buf[misalign:misalign + n]
     if n:
-        view.copy_(torch.from_numpy(np.ascontiguousarray(text)))
+        view.copy_(torch.from_numpy(np.array(text, dtype=np.uint8, copy=True)))
     return view
 
 
