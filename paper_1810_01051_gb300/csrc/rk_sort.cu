@@ -85,15 +85,23 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
-    // exclusive prefix of this pass's digit totals (thread d owns digit d)
+    // exclusive prefix of this pass's digit totals (thread d owns digit d):
+    // shuffle scan within each warp, then over the 8 warp totals
     uint32_t gbase;
     {
-        __shared__ uint32_t tot[256];
-        tot[tid] = ghist[tid];
+        __shared__ uint32_t wsum[kWarps];
+        const uint32_t v = ghist[tid];
+        uint32_t incl = v;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        uint32_t acc = 0;
-        for (uint32_t d = 0; d < tid; ++d) acc += tot[d];
-        gbase = acc;
+        uint32_t before = 0;
+        for (uint32_t w = 0; w < warp; ++w) before += wsum[w];
+        gbase = before + incl - v;
     }
     for (;;) {
         __syncthreads();
@@ -110,11 +118,16 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
         const uint64_t base = (uint64_t)tile * kSortTile + (uint64_t)warp * kPerWarp;
         uint64_t key[kPerWarp / 32];
         uint32_t rank[kPerWarp / 32];
+        // all of this warp's keys first (independent loads in flight together)
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+            const uint64_t idx = base + r * 32 + lane;
+            key[r] = idx < M ? __ldcg(in + idx) : 0;
+        }
 #pragma unroll
         for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
             const uint64_t idx = base + r * 32 + lane;
             const bool valid = idx < M;
-            key[r] = valid ? in[idx] : 0;
             const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t before = valid ? wcnt[warp][d] : 0;
@@ -138,26 +151,42 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
             *reinterpret_cast<volatile uint64_t *>(st) = kFlagInc | cnt;
         } else {
             *reinterpret_cast<volatile uint64_t *>(st) = kFlagAgg | cnt;
+            // read kWindow predecessors per step (loads in flight together),
+            // add their counts back to the first inclusive prefix
+            constexpr int kWindow = 16;
             int64_t j = (int64_t)tile - 1;
             uint64_t t0 = 0;
-            while (j >= 0) {
-                const uint64_t v = *reinterpret_cast<volatile const uint64_t *>(
-                    status + (uint64_t)j * 256u + tid);
-                if (v & kFlagInc) {
-                    excl += v & kCountMask;
-                    break;
+            bool done = false;
+            while (!done && j >= 0) {
+                uint64_t v[kWindow];
+#pragma unroll
+                for (int u = 0; u < kWindow; ++u)
+                    v[u] = j - u >= 0 ? *reinterpret_cast<volatile const uint64_t *>(
+                                            status + (uint64_t)(j - u) * 256u + tid)
+                                      : kFlagInc;
+                int consumed = 0;
+                bool stalled = false;
+#pragma unroll
+                for (int u = 0; u < kWindow; ++u) {
+                    if (done || stalled) continue;
+                    if (v[u] & kFlagInc) {
+                        excl += v[u] & kCountMask;
+                        done = true;
+                    } else if (v[u] & kFlagAgg) {
+                        excl += v[u] & kCountMask;
+                        ++consumed;
+                    } else {
+                        stalled = true;  // not published yet (claimed earlier, so it runs)
+                    }
                 }
-                if (v & kFlagAgg) {
-                    excl += v & kCountMask;
-                    --j;
-                    continue;
-                }
-                // predecessor not published yet (it was claimed earlier, so it runs)
-                if (t0 == 0) t0 = globaltimer_ns();
-                else if (globaltimer_ns() - t0 > kLookbackTimeoutNs) {
-                    info[1] = RK_ETIMEOUT;
-                    s_abort = 1;
-                    break;
+                j -= consumed;
+                if (stalled) {
+                    if (t0 == 0) t0 = globaltimer_ns();
+                    else if (globaltimer_ns() - t0 > kLookbackTimeoutNs) {
+                        info[1] = RK_ETIMEOUT;
+                        s_abort = 1;
+                        break;
+                    }
                 }
             }
             __threadfence();
@@ -215,7 +244,10 @@ int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, ui
 
     if (cudaMemsetAsync(ws + L.ctrl_off, 0, L.status_off - L.ctrl_off, stream) != cudaSuccess)
         return RK_ECUDA;
-    const uint32_t grid = (uint32_t)sm_count * 4;
+    // histogram grid: about one CTA per 4096 keys of the capacity, at most 4 per SM
+    const uint32_t grid =
+        (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count * 4,
+                                                           (capacity + 4095) / 4096));
     const uint64_t tiles = L.tiles;
     rk_sort_hist_kernel<<<grid, kThreads, 0, stream>>>(d_keys, info, capacity, sh, ghist, status,
                                                        tiles);

@@ -6,7 +6,7 @@
 
 namespace rk {
 
-constexpr uint32_t kSortTile = 4096;      // keys per tile of a sort pass
+constexpr uint32_t kSortTile = 2048;      // keys per tile of a sort pass
 constexpr uint32_t kMaxSortPasses = 8;    // 8-bit digits: 5 offset + 3 id digits at most
 
 struct SortWsLayout {
