@@ -77,7 +77,7 @@ typedef struct rk_build_opts {
                                   1 is the paper's shift-add base 2 */
     uint32_t filter;           /* RK_FILTER_* */
     uint32_t filter_log2_bits; /* prefilter size in bits, log2 (default: by pattern count) */
-    uint32_t warps;            /* consumer warps per CTA, 1..32 (default 16) */
+    uint32_t warps;            /* consumer warps per CTA, 1..31 (default 24) */
     uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16, <= 65536
                                   (default 49152) */
     uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */

@@ -32,13 +32,15 @@ struct GroupSlot {
 // One slot of the prefix map: a q-byte pattern prefix (little-endian value),
 // the run [first, first+count) of distinct pattern lengths in gram_lens, and
 // `ext`, a 32-bit fingerprint set of the next four bytes (bytes q..q+3) of
-// the patterns with this prefix that are at least q + 4 bytes long.
+// the patterns with this prefix that are at least q + 4 bytes long; bit 31 of
+// `count` (kGramShort) marks a prefix that also has a shorter pattern.
 struct GramSlot {
     uint32_t key;
     uint32_t first;
-    uint32_t count;  // 0 = empty slot
+    uint32_t count;  // 0 = empty slot; bit 31: some length is below q + 4
     uint32_t ext;
 };
+constexpr uint32_t kGramShort = 1u << 31;
 
 // Bit of `ext` for four bytes read as a little-endian word.
 __host__ __device__ __forceinline__ uint32_t ext_bit(uint32_t w) {

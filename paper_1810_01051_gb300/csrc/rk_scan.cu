@@ -195,6 +195,7 @@ cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uin
                        cudaStream_t st) {
     if (p.warps <= 8) return launch_w<MODE, Q4, 8>(p, grid, threads, smem, st);
     if (p.warps <= 16) return launch_w<MODE, Q4, 16>(p, grid, threads, smem, st);
+    if (p.warps <= 24) return launch_w<MODE, Q4, 24>(p, grid, threads, smem, st);
     return launch_w<MODE, Q4, 31>(p, grid, threads, smem, st);
 }
 

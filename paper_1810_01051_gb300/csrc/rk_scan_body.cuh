@@ -176,7 +176,9 @@ __device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w
         if (g.key == key) {
             // patterns of length >= q + 4 need bytes q..q+3 in the fingerprint set
             const bool ext_ok = (g.ext >> ext_bit((uint32_t)(v >> (8u * C.q)))) & 1u;
-            for (uint32_t j = 0; j < g.count; ++j) {
+            if (!ext_ok && !(g.count & kGramShort)) return;  // every length is >= q + 4
+            const uint32_t cnt = g.count & ~kGramShort;
+            for (uint32_t j = 0; j < cnt; ++j) {
                 const uint32_t L = C.s2.gram_lens[g.first + j];
                 if (x + L > C.n) break;  // lengths ascend
                 if (L >= C.q + 4 && !ext_ok) break;

@@ -140,7 +140,9 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
         uint32_t idx = (key * kGramMult) >> (32 - gram_bits);
         uint32_t mask = (1u << gram_bits) - 1;
         while (grams[idx].count) idx = (idx + 1) & mask;
-        grams[idx] = GramSlot{key, (uint32_t)gram_lens.size(), (uint32_t)v.size(), gram_ext[key]};
+        const uint32_t shorts = v.front() < q + 4 ? kGramShort : 0u;  // v ascends
+        grams[idx] = GramSlot{key, (uint32_t)gram_lens.size(), (uint32_t)v.size() | shorts,
+                              gram_ext[key]};
         gram_lens.insert(gram_lens.end(), v.begin(), v.end());
     }
 
@@ -301,8 +303,8 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     uint32_t base_log2 = o.base_log2 ? o.base_log2 : 8;
     if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
     if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
-    uint32_t warps = o.warps ? o.warps : 16;
-    // default: 48 KiB tiles (three 16 KiB rounds of 16 warps), two in flight
+    uint32_t warps = o.warps ? o.warps : 24;
+    // default: 48 KiB tiles (two 24 KiB rounds of 24 warps), two in flight
     uint32_t tile = o.tile_bytes ? o.tile_bytes : 49152;
     uint32_t stages = o.stages ? o.stages : 2;
     uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
