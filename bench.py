@@ -410,14 +410,6 @@ def measure_paper_kernel(torch, rk, dev, reps=5):
 
 # ---------------------------------------------------------------- our arm
 
-def sort_launches(n, k):
-    """Kernels of one sort: a histogram kernel, one kernel per 8-bit digit
-    pass, and a copy when the pass count is odd."""
-    def bits(v):
-        return int(v).bit_length()
-    passes = (bits(n - 1) + 7) // 8 + (bits(k - 1) + 7) // 8
-    return 1 + passes + (passes % 2)
-
 
 def run_ours(args, rank, world, local_rank):
     from oracle import build as oracle_build
@@ -464,6 +456,8 @@ def run_ours(args, rank, world, local_rank):
         if m <= cap:
             break
         cap = m + 1024
+
+    sort_kernels = rk.rk_sort_launches(table, n, cap)
 
     def step(evs=None):
         if evs:
@@ -585,7 +579,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": None if args.no_e2e else {
             "value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n,
             "d2h_bytes_per_step": 16 + 8 * m},
-        "gpu_launches": args.steps * (1 + sort_launches(n, k)),
+        "gpu_launches": args.steps * (1 + sort_kernels),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

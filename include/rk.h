@@ -138,11 +138,19 @@ int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_
 /* Sort the keys left by rk_scan_device ascending (= ascending (id, x)), in
  * place, reading the count from d_info on the device.  Does nothing when
  * d_info[0] > capacity.  n must be the text length given to the scan.
+ * Outputs of up to 8 tiles of 2048 keys per resident CTA are sorted by one
+ * cooperative launch (all digit passes, grid barriers between phases);
+ * larger ones by one decoupled look-back kernel per pass.
  *   d_workspace  at least rk_workspace_bytes(t, capacity) bytes, 16-byte aligned.
  * Errors: RK_EINVAL, RK_ECUDA.                                               */
 int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                    const uint64_t *d_info, void *d_workspace, uint64_t workspace_bytes,
                    void *stream);
+
+/* Kernels rk_sort_device launches on the current device for a text of n
+ * bytes and an output of `capacity` keys (the memory clear of its control
+ * words is not counted).  Errors: RK_EINVAL (t or launches NULL).           */
+int rk_sort_launches(const rk_table *t, uint64_t n, uint64_t capacity, uint32_t *launches);
 
 /* rk_scan_device followed by rk_sort_device on one stream: the sorted match
  * list of d_text[0..n) in d_keys, its length in d_info[0].                   */

@@ -78,6 +78,13 @@ extern "C" int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t
     return launch_scan(t, d_text, n, 0, n, d_keys, capacity, d_info, st);
 }
 
+extern "C" int rk_sort_launches(const rk_table *t, uint64_t n, uint64_t capacity,
+                                uint32_t *launches) {
+    if (!t || !launches) return RK_EINVAL;
+    *launches = sort_launches(t, n, capacity);
+    return RK_OK;
+}
+
 extern "C" int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                               const uint64_t *d_info, void *d_workspace, uint64_t workspace_bytes,
                               void *stream) {

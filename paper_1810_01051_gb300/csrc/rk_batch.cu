@@ -504,7 +504,7 @@ int enqueue(rk_batch *b, cudaStream_t st, bool scan_only) {
     uint32_t shifts[kMaxSortPasses], ns = 0;
     for (uint32_t s = 0; s < b->ob + b->pb + b->tb; s += 8) shifts[ns++] = s;
     int rc = launch_sort_shifts(b->sm_count, shifts, ns, b->d_keys, b->opts.capacity, b->d_info,
-                                b->d_ws, b->ws_bytes, st);
+                                b->d_ws, b->ws_bytes, st, false);
     if (rc) return rc;
     const uint32_t blocks = std::max<uint32_t>(1, (b->opts.max_items + 1 + 255) / 256);
     rk_batch_offsets_kernel<<<std::min<uint32_t>(blocks, 1024), 256, 0, st>>>(

@@ -163,12 +163,17 @@ int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capaci
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);
 
 // Sort keys[0 .. d_info[0]) ascending over the 8-bit digits at the given bit
-// shifts (least significant first).
+// shifts (least significant first).  allow_fused: outputs of up to 8 tiles
+// per resident CTA may be sorted by one cooperative launch (every pass, grid
+// barriers between phases) instead of one look-back kernel per pass.
 int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, uint64_t *d_keys,
                        uint64_t capacity, const uint64_t *d_info, void *d_ws, uint64_t ws_bytes,
-                       cudaStream_t stream);
+                       cudaStream_t stream, bool allow_fused);
 
 uint64_t sort_workspace_bytes(uint64_t capacity);
+
+// Kernels launch_sort starts for these arguments (on the current device).
+uint32_t sort_launches(const rk_table *t, uint64_t n, uint64_t capacity);
 
 int check_device(const rk_table *t);
 

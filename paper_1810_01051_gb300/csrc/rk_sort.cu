@@ -9,7 +9,7 @@
 //      digits (the totals do not depend on the order), and clears the
 //      per-tile status words of the passes;
 //   2. one kernel per pass: each CTA takes the next tile of 4096 keys from a
-//      counter, ranks its keys stably (warp match + per-warp digit counters),
+//      counter, ranks its keys stably (ballot multisplit + per-warp digit counters),
 //      publishes its digit counts, adds up the counts of the tiles before it
 //      by looking back through their published words (decoupled look-back),
 //      and scatters.  Look-back waits are bounded: a wait that runs out
@@ -17,6 +17,9 @@
 //
 // Every kernel reads the key count from d_info on the device, so nothing
 // returns to the host between the scan and the sorted list.
+#include <algorithm>
+#include <mutex>
+
 #include "rk_internal.cuh"
 #include "rk_sortws.cuh"
 
@@ -38,6 +41,20 @@ __device__ __forceinline__ bool sort_count(const unsigned long long *info, uint6
     *m = M;
     *tiles = (uint32_t)((M + kSortTile - 1) / kSortTile);
     return true;
+}
+
+// Lanes holding a valid key whose 8-bit digit equals this lane's: one ballot
+// per digit bit, a fixed cost whatever the number of distinct digits (a
+// warp match instruction takes longer the more distinct values there are).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (uint32_t b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
 }
 
 struct Shifts {
@@ -128,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
         for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
             const uint64_t idx = base + r * 32 + lane;
             const bool valid = idx < M;
-            const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+            const uint32_t peers = digit_peers(d, valid);
             const uint32_t before = valid ? wcnt[warp][d] : 0;
             rank[r] = before + __popc(peers & lt);
             __syncwarp();
@@ -206,6 +223,273 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
     }
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): one
+// arrival counter in global memory, target = barriers passed x CTAs.  The
+// wait is bounded; on a timeout RK_ETIMEOUT is recorded and false returned.
+__device__ __forceinline__ bool grid_sync(unsigned int *ctr, unsigned int target,
+                                          unsigned long long *info, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        uint64_t t0 = 0;
+        while (*reinterpret_cast<volatile unsigned int *>(ctr) < target) {
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kLookbackTimeoutNs) {
+                info[1] = RK_ETIMEOUT;
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Inclusive sum of v over the lanes up to this one.
+__device__ __forceinline__ uint32_t warp_incl(uint32_t v, uint32_t lane) {
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+// Stable ranks of one tile's keys (warp w: keys [w*256, (w+1)*256) of the
+// tile): key[r] and rank[r] per lane, the warp's digit counts in wc.
+__device__ __forceinline__ void rank_tile(const uint64_t *src, uint64_t M, uint64_t base,
+                                          uint32_t shift, uint64_t (&key)[kPerWarp / 32],
+                                          uint32_t (&rank)[kPerWarp / 32], uint32_t *wc,
+                                          uint32_t lane, uint32_t lt) {
+#pragma unroll
+    for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+        const uint64_t idx = base + r * 32 + lane;
+        key[r] = idx < M ? __ldcg(src + idx) : 0;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+        const bool valid = base + r * 32 + lane < M;
+        const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+        const uint32_t peers = digit_peers(d, valid);
+        const uint32_t bef = valid ? wc[d] : 0;
+        rank[r] = bef + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wc[d] = bef + __popc(peers);
+        __syncwarp();
+    }
+}
+
+// Every pass over a single tile (at most kSortTile keys) in one CTA: the keys
+// stay in registers (warp w: keys [w*256, (w+1)*256)), each pass ranks them,
+// scatters them to their place in the pass's order in shared memory and
+// reads them back.  No grid barrier, no global round trip between passes.
+__device__ __forceinline__ void sort_one_tile(uint64_t *keys, uint64_t M, const Shifts &sh,
+                                              uint64_t *sbuf, uint32_t (&wcnt)[kWarps][256],
+                                              uint32_t *dbase, uint32_t *wsum) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t base = warp * kPerWarp;
+    uint64_t key[kPerWarp / 32];
+    uint32_t rank[kPerWarp / 32];
+#pragma unroll
+    for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+        const uint32_t idx = base + r * 32 + lane;
+        key[r] = idx < M ? __ldcg(keys + idx) : 0;
+    }
+    for (uint32_t p = 0; p < sh.n; ++p) {
+        const uint32_t shift = sh.s[p];
+        for (uint32_t w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+            const bool valid = base + r * 32 + lane < M;
+            const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+            const uint32_t peers = digit_peers(d, valid);
+            const uint32_t bef = valid ? wcnt[warp][d] : 0;
+            rank[r] = bef + __popc(peers & lt);
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wcnt[warp][d] = bef + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t c = 0;  // digit tid: per-warp exclusive offsets, tile count
+        for (uint32_t w = 0; w < kWarps; ++w) {
+            const uint32_t x = wcnt[w][tid];
+            wcnt[w][tid] = c;
+            c += x;
+        }
+        const uint32_t incl = warp_incl(c, lane);
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (uint32_t w = 0; w < warp; ++w) before += wsum[w];
+        dbase[tid] = before + incl - c;
+        __syncthreads();
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r)
+            if (base + r * 32 + lane < M) {
+                const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+                sbuf[dbase[d] + wcnt[warp][d] + rank[r]] = key[r];
+            }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t r = 0; r < kPerWarp / 32; ++r)
+            if (base + r * 32 + lane < M) key[r] = sbuf[base + r * 32 + lane];
+        __syncthreads();
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+        const uint32_t idx = base + r * 32 + lane;
+        if (idx < M) keys[idx] = key[r];
+    }
+}
+
+// Every pass in one cooperative launch, for outputs of a few thousand tiles.
+// cnt holds, digit-major, the count of digit d among the keys of tile t at
+// [d * pitch + t].  Per pass:
+//   A  each CTA ranks its tile's keys stably (per-warp digit counters) and
+//      publishes the tile's digit counts;
+//   B  one warp per digit turns its row into exclusive prefixes over the
+//      tiles (in place) and a total;
+//   C  each CTA scatters its keys to (start of the digit) + (prefix of the
+//      tile) + (rank within the tile);
+// with a grid barrier after each phase.  With one tile per CTA the keys,
+// ranks and counters stay on chip from A to C; with more, C ranks again.
+// A single tile is sorted by one CTA alone, without barriers.
+// A fixed number of barriers replaces the chain of look-back waits, whose
+// length grows with the tile count.  An odd pass count ends with a copy
+// back from the second buffer.  CTAs beyond the tile count leave at once.
+__global__ void __launch_bounds__(kThreads) rk_sort_fused_kernel(
+    uint64_t *keys, uint64_t *tmp, unsigned long long *info, uint64_t cap, Shifts sh,
+    uint32_t *cnt, uint32_t pitch, uint32_t *totals, unsigned int *bar) {
+    uint64_t M;
+    uint32_t T;
+    if (!sort_count(info, cap, &M, &T)) return;
+    const uint32_t G = min(gridDim.x, T);  // CTAs taking part
+    if (blockIdx.x >= G) return;
+    __shared__ uint32_t wcnt[kWarps][256];
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wsum[kWarps];
+    __shared__ int s_ok;
+    if (T == 1) {
+        __shared__ uint64_t sbuf[kSortTile];
+        sort_one_tile(keys, M, sh, sbuf, wcnt, dbase, wsum);
+        return;
+    }
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const bool one = T <= G;  // one tile per CTA: state kept from A to C
+    unsigned int passed = 0;
+    uint64_t key[kPerWarp / 32];
+    uint32_t rank[kPerWarp / 32];
+    for (uint32_t p = 0; p < sh.n; ++p) {
+        const uint64_t *src = (p & 1) ? tmp : keys;
+        uint64_t *dst = (p & 1) ? keys : tmp;
+        const uint32_t shift = sh.s[p];
+
+        // A: rank each tile, publish its digit counts
+        for (uint32_t t = blockIdx.x; t < T; t += G) {
+            for (uint32_t w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+            __syncthreads();
+            rank_tile(src, M, (uint64_t)t * kSortTile + (uint64_t)warp * kPerWarp, shift, key,
+                      rank, wcnt[warp], lane, lt);
+            __syncthreads();
+            uint32_t c = 0;
+            for (uint32_t w = 0; w < kWarps; ++w) c += wcnt[w][tid];
+            cnt[(uint64_t)tid * pitch + t] = c;
+            __syncthreads();
+        }
+        if (!grid_sync(bar, ++passed * G, info, &s_ok)) return;
+
+        // B: per digit, exclusive prefix over the tiles (in place) and total:
+        // under 32 tiles one thread per digit (its loads issued together),
+        // else one warp per digit (256 warps or more take part)
+        if (T < 32) {
+            if (blockIdx.x == 0) {
+                uint32_t *row = cnt + (uint64_t)tid * pitch;
+                uint32_t v[32];
+#pragma unroll
+                for (uint32_t t = 0; t < 32; ++t) v[t] = t < T ? __ldcg(row + t) : 0u;
+                uint32_t sum = 0;
+#pragma unroll
+                for (uint32_t t = 0; t < 32; ++t)
+                    if (t < T) {
+                        row[t] = sum;
+                        sum += v[t];
+                    }
+                totals[tid] = sum;
+            }
+        } else
+        for (uint32_t d = blockIdx.x * kWarps + warp; d < 256; d += G * kWarps) {
+            uint32_t *row = cnt + (uint64_t)d * pitch;
+            uint32_t carry = 0;
+            for (uint32_t t0 = 0; t0 < T; t0 += 8 * 32) {
+                uint32_t v[8];
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) {
+                    const uint32_t t = t0 + 32 * j + lane;
+                    v[j] = t < T ? __ldcg(row + t) : 0u;
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) {
+                    const uint32_t t = t0 + 32 * j + lane;
+                    const uint32_t incl = warp_incl(v[j], lane);
+                    if (t < T) row[t] = carry + incl - v[j];
+                    carry += __shfl_sync(0xffffffffu, incl, 31);
+                }
+            }
+            if (lane == 0) totals[d] = carry;
+        }
+        if (!grid_sync(bar, ++passed * G, info, &s_ok)) return;
+
+        // C: scatter
+        for (uint32_t t = blockIdx.x; t < T; t += G) {
+            const uint32_t tot = __ldcg(totals + tid);
+            const uint32_t tpre = __ldcg(cnt + (uint64_t)tid * pitch + t);
+            const uint64_t base = (uint64_t)t * kSortTile + (uint64_t)warp * kPerWarp;
+            if (!one) {
+                for (uint32_t w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+                __syncthreads();
+                rank_tile(src, M, base, shift, key, rank, wcnt[warp], lane, lt);
+                __syncthreads();
+            }
+            // per-warp exclusive offsets of digit tid within the tile
+            uint32_t c = 0;
+            for (uint32_t w = 0; w < kWarps; ++w) {
+                const uint32_t x = wcnt[w][tid];
+                wcnt[w][tid] = c;
+                c += x;
+            }
+            const uint32_t incl = warp_incl(tot, lane);
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            uint32_t before = 0;
+            for (uint32_t w = 0; w < warp; ++w) before += wsum[w];
+            dbase[tid] = before + incl - tot + tpre;
+            __syncthreads();
+#pragma unroll
+            for (uint32_t r = 0; r < kPerWarp / 32; ++r) {
+                if (base + r * 32 + lane < M) {
+                    const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+                    dst[dbase[d] + wcnt[warp][d] + rank[r]] = key[r];
+                }
+            }
+            __syncthreads();
+        }
+        if (p + 1 < sh.n || (sh.n & 1))
+            if (!grid_sync(bar, ++passed * G, info, &s_ok)) return;
+    }
+    if (sh.n & 1)
+        for (uint64_t i = blockIdx.x * (uint64_t)kThreads + tid; i < M; i += (uint64_t)G * kThreads)
+            keys[i] = __ldcg(tmp + i);
+}
+
 __global__ void rk_sort_copy_kernel(const uint64_t *in, uint64_t *out,
                                     const unsigned long long *info, uint64_t cap) {
     uint64_t M;
@@ -222,13 +506,52 @@ uint32_t bits_for(uint64_t max_value) {
     return b;
 }
 
+// CTAs of the fused sort: at most two per SM, all resident (0: the kernel
+// does not fit on this device).
+uint32_t fused_grid(int sm_count) {
+    static std::mutex mu;
+    static int dev_seen[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    static uint32_t per_sm[8];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 8) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev_seen[dev] != dev) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rk_sort_fused_kernel, kThreads, 0) !=
+            cudaSuccess)
+            nb = 0;
+        per_sm[dev] = (uint32_t)std::max(0, std::min(nb, 2));
+        dev_seen[dev] = dev;
+    }
+    return per_sm[dev] * (uint32_t)sm_count;
+}
+
+// CTAs of the fused sort for an output of `capacity` keys (0: the look-back
+// kernels are used instead).
+uint32_t fused_ctas(int sm_count, uint64_t capacity, bool allow_fused) {
+    const uint32_t gmax = allow_fused ? fused_grid(sm_count) : 0;
+    const uint64_t tiles = sort_ws_layout(capacity).tiles;
+    if (!gmax || tiles > 8ull * gmax) return 0;
+    return (uint32_t)std::min<uint64_t>(tiles, gmax);
+}
+
+// The digit shifts of a plain search's keys: the offset field's bits below
+// ceil(log2(n)), then the id field's bits up to ceil(log2(k)).
+uint32_t plain_shifts(uint64_t n, uint32_t k, uint32_t *shifts) {
+    uint32_t ns = 0;
+    const uint32_t ob = bits_for(n - 1), pb = bits_for(k - 1);
+    for (uint32_t s = 0; s < ob; s += 8) shifts[ns++] = s;
+    for (uint32_t s = 0; s < pb; s += 8) shifts[ns++] = RK_KEY_OFFSET_BITS + s;
+    return ns;
+}
+
 }  // namespace
 
 uint64_t sort_workspace_bytes(uint64_t capacity) { return sort_ws_bytes(capacity); }
 
 int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, uint64_t *d_keys,
                        uint64_t capacity, const uint64_t *d_info, void *d_ws, uint64_t ws_bytes,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, bool allow_fused) {
     if (capacity < 2 || nshift == 0) return RK_OK;
     if (nshift > kMaxSortPasses || ws_bytes < sort_ws_bytes(capacity)) return RK_EINVAL;
     const SortWsLayout L = sort_ws_layout(capacity);
@@ -244,6 +567,21 @@ int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, ui
 
     if (cudaMemsetAsync(ws + L.ctrl_off, 0, L.status_off - L.ctrl_off, stream) != cudaSuccess)
         return RK_ECUDA;
+    // up to 8 tiles per CTA: every pass in one cooperative launch
+    if (const uint32_t g = fused_ctas(sm_count, capacity, allow_fused)) {
+        // digit-major counts, 256 x tiles (in the look-back words' space)
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(status);
+        uint32_t pitch = (uint32_t)L.tiles;
+        uint32_t *totals = ghist;
+        unsigned int *bar = counters + 32;
+        void *args[] = {&d_keys, &tmp, &info, &capacity, &sh, &cnt, &pitch, &totals, &bar};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(rk_sort_fused_kernel), g,
+                                        kThreads, args, 0, stream) != cudaSuccess) {
+            cudaGetLastError();
+            return RK_ECUDA;
+        }
+        return RK_OK;
+    }
     // histogram grid: about one CTA per 4096 keys of the capacity, at most 4 per SM
     const uint32_t grid =
         (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count * 4,
@@ -267,12 +605,19 @@ int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, ui
 int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream) {
     if (n == 0 || t->dev.n_patterns == 0) return RK_OK;
-    uint32_t shifts[kMaxSortPasses], ns = 0;
-    const uint32_t ob = bits_for(n - 1), pb = bits_for(t->dev.n_patterns - 1);
-    for (uint32_t s = 0; s < ob; s += 8) shifts[ns++] = s;
-    for (uint32_t s = 0; s < pb; s += 8) shifts[ns++] = RK_KEY_OFFSET_BITS + s;
+    uint32_t shifts[kMaxSortPasses];
+    const uint32_t ns = plain_shifts(n, t->dev.n_patterns, shifts);
     return launch_sort_shifts(t->sm_count, shifts, ns, d_keys, capacity, d_info, d_ws, ws_bytes,
-                              stream);
+                              stream, true);
+}
+
+uint32_t sort_launches(const rk_table *t, uint64_t n, uint64_t capacity) {
+    if (n == 0 || t->dev.n_patterns == 0 || capacity < 2) return 0;
+    uint32_t shifts[kMaxSortPasses];
+    const uint32_t ns = plain_shifts(n, t->dev.n_patterns, shifts);
+    if (ns == 0) return 0;
+    if (fused_ctas(t->sm_count, capacity, true)) return 1;
+    return 1 + ns + (ns & 1);  // histogram, one kernel per pass, copy back
 }
 
 }  // namespace rk

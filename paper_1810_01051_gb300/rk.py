@@ -28,6 +28,7 @@ RK_NOALLOC_MAX_KEYS = 1 << 20
 #: names of every function include/rk.h declares
 EXPORTS = [
     "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
+    "rk_sort_launches",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
     "rk_window_hashes_device", "rk_search_device_noalloc",
     "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
@@ -114,6 +115,8 @@ def load() -> ctypes.CDLL:
     L.rk_table_info_get.argtypes = [vp, ctypes.POINTER(TableInfo)]
     L.rk_workspace_bytes.restype = u64
     L.rk_workspace_bytes.argtypes = [vp, u64]
+    L.rk_sort_launches.restype = ctypes.c_int
+    L.rk_sort_launches.argtypes = [vp, u64, u64, ctypes.POINTER(u32)]
     L.rk_scan_device.restype = ctypes.c_int
     L.rk_scan_device.argtypes = [vp, vp, u64, vp, u64, vp, vp]
     L.rk_sort_device.restype = ctypes.c_int
@@ -224,6 +227,15 @@ def rk_table_info(table: int) -> dict:
 
 def rk_workspace_bytes(table: int, capacity: int) -> int:
     return int(load().rk_workspace_bytes(table, capacity))
+
+
+def rk_sort_launches(table: int, n: int, capacity: int) -> int:
+    """Kernels rk_sort_device launches for a text of n bytes and `capacity` keys."""
+    out = ctypes.c_uint32(0)
+    rc = load().rk_sort_launches(table, n, capacity, ctypes.byref(out))
+    if rc != RK_OK:
+        raise RuntimeError(f"rk_sort_launches: {strerror(rc)}")
+    return int(out.value)
 
 
 def rk_scan_device(table: int, d_text, n: int, d_keys, capacity: int, d_info,

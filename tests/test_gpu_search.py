@@ -173,3 +173,28 @@ def test_scan_then_sort_equals_search():
         assert_same(rk.unpack_keys(srt), oracle.rabin_karp(w.text, w.patterns), "scan+sort")
     finally:
         rk.rk_destroy(table)
+
+
+@pytest.mark.parametrize("n,k,lmin,lmax", [(1 << 20, 12, 2, 6), ((1 << 22) + 5, 300, 8, 12)],
+                         ids=["4-passes", "5-passes"])
+def test_sort_paths_agree(n, k, lmin, lmax):
+    """The cooperative single-launch sort (small capacity) and the per-pass
+    look-back kernels (capacity beyond 8 tiles per resident CTA) give the
+    oracle's list on the same keys, with odd and even pass counts and with
+    several tiles per CTA (more than two tiles per SM of matches)."""
+    torch = pytest.importorskip("torch")
+    w = random_small(77 + k, n, k, lmin, lmax, alphabet=b"ab", plants=0)
+    expect = oracle.rabin_karp(w.text, w.patterns)
+    m = int(expect[0].size)
+    assert m > 2048 * 2 * 152, m  # more tiles than resident CTAs of the fused sort
+    table = rk.rk_build(w.patterns)
+    try:
+        d = to_device(w.text)
+        for cap, fused in ((m + 100, True), (1 << 24, False)):
+            launches = rk.rk_sort_launches(table, n, cap)
+            assert (launches == 1) == fused, (cap, launches)
+            keys, count, status = search_table(table, d, n, cap)
+            assert status == rk.RK_OK and count == m
+            assert_same(keys_to_pairs(keys[:count]), expect, f"cap {cap}")
+    finally:
+        rk.rk_destroy(table)
