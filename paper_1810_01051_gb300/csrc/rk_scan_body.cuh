@@ -11,12 +11,14 @@
 namespace rk {
 
 // 8 bytes starting at any position of a 16-byte aligned shared buffer,
-// little-endian (byte i of the window in bits 8i..8i+7).
+// little-endian (byte i of the window in bits 8i..8i+7): three aligned words
+// and two funnel shifts (reads at most 4 bytes past the 8).
 __device__ __forceinline__ uint64_t ld8(const uint8_t *buf, uint32_t pos) {
-    uint32_t a = pos & ~7u, s = (pos & 7u) * 8u;
-    uint64_t lo = *reinterpret_cast<const uint64_t *>(buf + a);
-    uint64_t hi = *reinterpret_cast<const uint64_t *>(buf + a + 8);
-    return s ? (lo >> s) | (hi << (64u - s)) : lo;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(buf + (pos & ~3u));
+    const uint32_t s = (pos & 3u) * 8u;
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+    const uint32_t lo = __funnelshift_r(w0, w1, s), hi = __funnelshift_r(w1, w2, s);
+    return ((uint64_t)hi << 32) | lo;
 }
 
 // Rabin hash of buf[pos .. pos+L) mod 2^61-1 with B = 2^k.
