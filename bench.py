@@ -37,7 +37,9 @@ sys.path.insert(0, ROOT)
 METRIC = "text GB/s scanned (plain single-text multi-pattern search, sorted match list)"
 UNIT = "GB/s"
 WORKLOAD = "zipf_text_1GiB_100_patterns_len4-32_density1e-6"
-SCAN_SRC = os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", "rk_scan.cu")
+# the sources the scan kernel is compiled from (the profile records their hash)
+SCAN_SRCS = [os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", f)
+             for f in ("rk_scan.cu", "rk_scan_body.cuh", "rk_layout.cuh", "rk_internal.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "rk_scan_zipf_1GiB.md")
 CPU_SAMPLE_PER_CORE = 8 << 20   # bytes per core for the oracle baseline
 SLICE_HALO_NOTE = "each slice carries (longest pattern - 1) extra bytes"
@@ -79,19 +81,37 @@ def time_oracle(pool, slices, patterns):
     return time.perf_counter() - t0
 
 
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of the GB300s, else
+    the fallback figure of one earlier measurement."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def scan_sources_sha256():
+    """SHA-256 of the scan kernel's sources, concatenated in SCAN_SRCS order."""
+    h = hashlib.sha256()
+    for f in SCAN_SRCS:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def read_profile_traffic():
     """DRAM bytes per scan launch from the committed ncu summary, if it was
-    taken on the current scan kernel source (else None)."""
+    taken on the current scan kernel sources (else None)."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
-    m_src = re.search(r"scan_source_sha256:\s*([0-9a-f]{64})", txt)
+    m_src = re.search(r"scan_sources_sha256:\s*([0-9a-f]{64})", txt)
     m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     if not (m_src and m_tr):
         return None
-    cur = hashlib.sha256(open(SCAN_SRC, "rb").read()).hexdigest()
-    return float(m_tr.group(1)) if m_src.group(1) == cur else None
+    return float(m_tr.group(1)) if m_src.group(1) == scan_sources_sha256() else None
 
 
 class ClockSampler:
@@ -408,6 +428,52 @@ def measure_paper_kernel(torch, rk, dev, reps=5):
     return out
 
 
+def measure_plain_configs(torch, rk, dev, hbm_gbs, reps=5):
+    """The other two plain configurations (the bench line itself is the Zipf
+    scan): searches (scan + sort) over the resident text, timed with CUDA
+    events; GB/s = text bytes / search time, and the scan alone against the
+    HBM peak (text read once + 8 bytes per match)."""
+    from workloads import make_config
+    st = torch.cuda.Stream(dev)
+    out = {}
+    for i, name in ((0, "dna_1MiB_8x16"), (2, "signature_set_4GiB_10000x8-64")):
+        w = make_config(i)
+        d = torch.from_numpy(w.text).to(dev)
+        table = rk.rk_build(w.patterns)
+        cap = 1 << 16
+        while True:
+            keys = torch.empty(cap, dtype=torch.int64, device=dev)
+            info = torch.zeros(2, dtype=torch.int64, device=dev)
+            wsb = rk.rk_workspace_bytes(table, cap)
+            ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            rk.rk_search_device(table, d, w.n, keys, cap, info, ws, wsb, st)
+            st.synchronize()
+            m = int(info[0])
+            if m <= cap:
+                break
+            cap = m + 1024
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        scan_ms, search_ms = [], []
+        for _ in range(reps + 1):
+            ev[0].record(st)
+            rk.rk_scan_device(table, d, w.n, keys, cap, info, st)
+            ev[1].record(st)
+            rk.rk_sort_device(table, w.n, keys, cap, info, ws, wsb, st)
+            ev[2].record(st)
+            st.synchronize()
+            scan_ms.append(ev[0].elapsed_time(ev[1]))
+            search_ms.append(ev[0].elapsed_time(ev[2]))
+        scan = statistics.median(scan_ms[1:])
+        search = statistics.median(search_ms[1:])
+        out[name] = {"text_bytes": w.n, "patterns": len(w.patterns), "matches": m,
+                     "search_ms": search, "gbps": w.n / search / 1e6,
+                     "scan_ms": scan, "scan_gbps_algorithmic": (w.n + 8 * m) / scan / 1e6,
+                     "scan_frac_of_hbm": (w.n + 8 * m) / scan / 1e6 / hbm_gbs}
+        rk.rk_destroy(table)
+        del d, keys, ws
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 
@@ -519,7 +585,9 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_extras:
         for name, fn in (("batched", lambda: measure_batched(torch, rk, dev, 2 << 20)),
                          ("served", lambda: measure_serving(torch, rk, dev)),
-                         ("paper_kernel", lambda: measure_paper_kernel(torch, rk, dev))):
+                         ("paper_kernel", lambda: measure_paper_kernel(torch, rk, dev)),
+                         ("plain_configs",
+                          lambda: measure_plain_configs(torch, rk, dev, hbm_peak()[0]))):
             try:
                 extra[name] = fn()
             except Exception as exc:  # a failed extra must not lose the main line
@@ -540,11 +608,7 @@ def run_ours(args, rank, world, local_rank):
     value = world * n * args.steps / (total_ms / 1e3) / 1e9
     scan_mean_s = statistics.mean(scan_ms) / 1e3
     alg_bytes = n + 8 * m
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = hbm_peak()
     achieved = alg_bytes / scan_mean_s / 1e9
     traffic = read_profile_traffic()
 
