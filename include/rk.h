@@ -152,8 +152,33 @@ int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t cap
  * words is not counted).  Errors: RK_EINVAL (t or launches NULL).           */
 int rk_sort_launches(const rk_table *t, uint64_t n, uint64_t capacity, uint32_t *launches);
 
+/* Bytes of device workspace rk_scan_device_ws needs for a text of n bytes:
+ * a candidate count and a list of up to n / 64 + 4096 candidates, 8 bytes
+ * each (0 on bad arguments). */
+uint64_t rk_scan_workspace_bytes(const rk_table *t, uint64_t n);
+
+/* rk_scan_device with the survivors' Rabin hash, table probe and byte
+ * comparison (Section 3.1's hx == hy test and compare(P, T + x, m)) moved to
+ * a second kernel: the tiled scan only lists each window whose exact q-byte
+ * prefix starts some pattern and whose next four bytes pass that prefix's
+ * fingerprint set; the second kernel takes the list 32 windows per warp and
+ * reads them from d_text.  Same match set as rk_scan_device (the order of
+ * the unsorted keys differs).  Windows offered beyond the list's room are
+ * verified inside the scan as rk_scan_device does.
+ *   d_workspace  at least rk_scan_workspace_bytes(t, n) bytes, 16-byte
+ *                aligned, not shared with a call in flight; a smaller (or
+ *                null) workspace, or a table built with RK_FILTER_NONE,
+ *                runs rk_scan_device instead.
+ * Other arguments, results and errors as rk_scan_device.                    */
+int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
+                      uint64_t capacity, uint64_t *d_info, void *d_workspace,
+                      uint64_t workspace_bytes, void *stream);
+
 /* rk_scan_device followed by rk_sort_device on one stream: the sorted match
- * list of d_text[0..n) in d_keys, its length in d_info[0].                   */
+ * list of d_text[0..n) in d_keys, its length in d_info[0].  A workspace of
+ * rk_workspace_bytes(t, capacity) + rk_scan_workspace_bytes(t, n) bytes
+ * makes the scan part run as rk_scan_device_ws (its list placed after the
+ * sort's workspace).                                                         */
 int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
                      uint64_t capacity, uint64_t *d_info, void *d_workspace,
                      uint64_t workspace_bytes, void *stream);

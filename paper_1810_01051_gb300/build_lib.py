@@ -21,7 +21,7 @@ LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "librk.so")
 
 SOURCES = ["rk_table.cu", "rk_scan.cu", "rk_sort.cu", "rk_api.cu", "rk_noalloc.cu",
-           "rk_batch.cu", "rk_server.cu", "rk_paper.cu"]
+           "rk_batch.cu", "rk_server.cu", "rk_paper.cu", "rk_verify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                  f"-I{INCLUDE}", f"-I{CSRC}"]

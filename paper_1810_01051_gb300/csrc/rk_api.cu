@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "rk_internal.cuh"
+#include "rk_sortws.cuh"
 
 using namespace rk;
 
@@ -68,6 +69,49 @@ extern "C" uint64_t rk_workspace_bytes(const rk_table *t, uint64_t capacity) {
     return sort_workspace_bytes(capacity);
 }
 
+extern "C" uint64_t rk_scan_workspace_bytes(const rk_table *t, uint64_t n) {
+    if (!t || n > RK_MAX_TEXT_LEN) return 0;
+    return scan_ws_layout(n).total;
+}
+
+namespace {
+
+// The candidate list inside a deferred scan's workspace (null: too small, or
+// a table that cannot defer).
+bool cand_list(const rk_table *t, uint64_t n, void *ws, uint64_t ws_bytes, CandList *cl) {
+    const ScanWsLayout L = scan_ws_layout(n);
+    if (!can_defer(t) || !ws || !aligned(ws, 16) || ws_bytes < L.total) return false;
+    uint8_t *b = reinterpret_cast<uint8_t *>(ws);
+    *cl = CandList{reinterpret_cast<uint64_t *>(b + L.list_off), L.cap,
+                   reinterpret_cast<unsigned long long *>(b + L.count_off)};
+    return true;
+}
+
+// Scan with the survivors' hash/probe/verify in a second kernel.
+int deferred_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
+                  uint64_t capacity, uint64_t *d_info, const CandList &cl, cudaStream_t st) {
+    if (cudaMemsetAsync(d_info, 0, 2 * sizeof(uint64_t), st) != cudaSuccess ||
+        cudaMemsetAsync(cl.count, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return RK_ECUDA;
+    int rc = launch_scan(t, d_text, n, 0, n, d_keys, capacity, d_info, st, &cl);
+    if (rc) return rc;
+    return launch_verify(t, d_text, n, cl, d_keys, capacity, d_info, st);
+}
+
+}  // namespace
+
+extern "C" int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                                 uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                                 void *d_workspace, uint64_t workspace_bytes, void *stream) {
+    int rc = scan_args_ok(t, d_text, n, d_keys, capacity, d_info);
+    if (rc) return rc;
+    CandList cl;
+    if (!cand_list(t, n, d_workspace, workspace_bytes, &cl))
+        return rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
+    return deferred_scan(t, d_text, n, d_keys, capacity, d_info, cl,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n,
                               uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
                               void *stream) {
@@ -108,7 +152,17 @@ extern "C" int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64
     if (capacity >= 2 && (!d_workspace || !aligned(d_workspace, 16) ||
                           workspace_bytes < sort_workspace_bytes(capacity)))
         return RK_EINVAL;
-    rc = rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
+    // a workspace that also holds a scan workspace after the sort's defers
+    // the survivors' verification to a second kernel
+    const uint64_t sort_bytes = capacity >= 2 ? sort_workspace_bytes(capacity) : 0;
+    CandList cl;
+    if (d_workspace && workspace_bytes > sort_bytes &&
+        cand_list(t, n, reinterpret_cast<uint8_t *>(d_workspace) + sort_bytes,
+                  workspace_bytes - sort_bytes, &cl))
+        rc = deferred_scan(t, d_text, n, d_keys, capacity, d_info, cl,
+                           reinterpret_cast<cudaStream_t>(stream));
+    else
+        rc = rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
     if (rc) return rc;
     return launch_sort(t, n, d_keys, capacity, d_info, d_workspace, workspace_bytes,
                        reinterpret_cast<cudaStream_t>(stream));
@@ -137,7 +191,13 @@ extern "C" int rk_search(const rk_table *tc, const uint8_t *h_text, uint64_t n, 
     t->h_keys_cap = cap_bytes;
     uint64_t info_cap = t->h_info ? 16 : 0;
     if ((rc = ensure(reinterpret_cast<void **>(&t->h_info), &info_cap, 16))) return rc;
-    if ((rc = ensure(&t->h_ws, &t->h_ws_cap, sort_workspace_bytes(kcap)))) return rc;
+    // sort workspace, then the deferred scan's candidate list
+    const uint64_t sort_bytes = sort_workspace_bytes(kcap);
+    const uint64_t scan_bytes = can_defer(t) ? scan_ws_layout(n).total : 0;
+    if ((rc = ensure(&t->h_ws, &t->h_ws_cap, sort_bytes + scan_bytes))) return rc;
+    CandList cl;
+    const bool defer = scan_bytes && cand_list(t, n, reinterpret_cast<uint8_t *>(t->h_ws) + sort_bytes,
+                                               scan_bytes, &cl);
 
     // Copy the text in chunks on one stream while the other scans the windows
     // whose bytes (window + longest pattern - 1) have arrived.
@@ -149,7 +209,8 @@ extern "C" int rk_search(const rk_table *tc, const uint8_t *h_text, uint64_t n, 
         t->events.push_back(e);
     }
     cudaStream_t sc = t->s_comp, sx = t->s_copy;
-    bool ok = cudaMemsetAsync(t->h_info, 0, 16, sc) == cudaSuccess;
+    bool ok = cudaMemsetAsync(t->h_info, 0, 16, sc) == cudaSuccess &&
+              (!defer || cudaMemsetAsync(cl.count, 0, 8, sc) == cudaSuccess);
     for (uint64_t c = 0; ok && c < nchunks; ++c) {
         uint64_t b = c * chunk, e = std::min(n, b + chunk);
         ok = cudaMemcpyAsync(t->h_text + b, h_text + b, e - b, cudaMemcpyHostToDevice, sx) ==
@@ -162,9 +223,13 @@ extern "C" int rk_search(const rk_table *tc, const uint8_t *h_text, uint64_t n, 
         uint64_t need = std::min(n, e + reach);                  // last byte a window may read
         uint64_t last = need ? (need - 1) / chunk : 0;          // chunk holding it
         ok = cudaStreamWaitEvent(sc, t->events[last], 0) == cudaSuccess;
-        if (ok && launch_scan(t, t->h_text, n, b, e, t->h_keys, capacity, t->h_info, sc) != RK_OK)
+        if (ok && launch_scan(t, t->h_text, n, b, e, t->h_keys, capacity, t->h_info, sc,
+                              defer ? &cl : nullptr) != RK_OK)
             ok = false;
     }
+    if (ok && defer &&
+        launch_verify(t, t->h_text, n, cl, t->h_keys, capacity, t->h_info, sc) != RK_OK)
+        ok = false;
     if (!ok) {
         cudaStreamSynchronize(sx);
         cudaStreamSynchronize(sc);

@@ -147,17 +147,37 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
                uint32_t filter_opt, uint32_t filter_bits_opt, TableBlob *out);
 void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dev_base);
 
+// Candidate list of a scan whose survivors are verified in a second pass
+// (entries: text offset | prefix-map slot << 40).
+struct CandList {
+    uint64_t *list;
+    uint64_t cap;
+    unsigned long long *count;  // candidates offered (zeroed before the scan; may exceed cap)
+};
+
 // Scan windows whose start x lies in [x_begin, x_end) of a text of n bytes
 // (bytes up to min(n, x_end + lmax - 1) must be resident); adds to d_info.
 int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
                 uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
-                cudaStream_t stream);
+                cudaStream_t stream, const CandList *cand = nullptr);
 
 // launch_scan with an explicit wait limit; `withhold` makes the producer
-// issue no copy (diagnostics: every consumer wait then runs out).
+// issue no copy (diagnostics: every consumer wait then runs out).  With a
+// candidate list (can_defer(t) only), survivors stop after the prefix-map
+// lookup and their candidates go to the list; launch_verify completes them.
 int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
                      uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
-                     cudaStream_t stream, uint64_t timeout_ns, bool withhold);
+                     cudaStream_t stream, uint64_t timeout_ns, bool withhold,
+                     const CandList *cand = nullptr);
+
+// Tables whose survivors can be verified in a second pass: a stage-1 filter
+// and prefix-map slot indices below 2^24.
+bool can_defer(const rk_table *t);
+
+// Hash, probe and verify every listed candidate of a deferred scan of
+// d_text[0..n); matches are added to d_keys / d_info.
+int launch_verify(const rk_table *t, const uint8_t *d_text, uint64_t n, const CandList &cand,
+                  uint64_t *d_keys, uint64_t capacity, uint64_t *d_info, cudaStream_t stream);
 
 int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capacity,
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);

@@ -53,17 +53,23 @@ struct ScanParams {
     uint64_t timeout_ns;     // limit of every pipeline wait
     uint32_t tile, stages, halo, warps, s2_smem;
     uint32_t withhold;       // diagnostics: the producer issues no copy at all
+    uint64_t *cand;          // deferred verification: candidate list (DEFER kernels)
+    uint64_t cand_cap;
+    unsigned long long *cand_count;
 };
 
 // MAXW: most consumer warps this instance is launched with; the register
 // budget per thread follows from (MAXW + 1) warps per SM.  S2S: the
 // survivor-stage tables are staged in shared memory (their loads then
-// compile to shared-memory loads).
-template <int MODE, bool Q4, int MAXW, bool S2S>
+// compile to shared-memory loads).  DEFER: survivors stop after the
+// prefix-map stage and go to the candidate list (verified by
+// rk_verify_kernel).
+template <int MODE, bool Q4, int MAXW, bool S2S, bool DEFER>
 __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ volatile uint32_t s_abort;
+    __shared__ uint32_t s_direct[32];  // DEFER: saturated counters, emit() goes to global memory
     const SmemLayout lay =
         smem_layout(P.tab.filter_bytes, P.s2_smem, P.warps, P.stages, P.tile, P.halo);
     uint8_t *sfilt = smem;  // the bit set is first (offset 0): its base folds into addresses
@@ -97,6 +103,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         fence_mbar_init();
     }
     if (tid < nw) mcount[tid] = 0;
+    if (DEFER && tid < nw) s_direct[tid] = 0x80000000u;
     __syncthreads();
 
     const uint64_t my_tiles =
@@ -144,6 +151,8 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     C.n_lengths = P.tab.n_lengths;
     uint16_t *q = queues + warp * kQueueCap;
     WarpCtx w{mcount + warp, mbuf + (size_t)warp * kMatchCap, P.keys, P.capacity, P.info};
+    const WarpCtx wm{s_direct + warp, nullptr, P.keys, P.capacity, P.info};
+    const CandList cc{P.cand, P.cand_cap, P.cand_count};
     const uint32_t lane4 = lane << 2;
     const uint32_t fmask = P.tab.filter_mask;
     const uint32_t qmask = P.tab.q == 4 ? 0xFFFFFFFFu : (1u << (8u * P.tab.q)) - 1u;
@@ -161,18 +170,18 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         const uint64_t u0 = P.u_first + t * P.tile;
         const uint64_t wend = min(u0 + P.tile, C.hi);
         const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
-        consume_tile<MODE, Q4>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4, qmask, warp,
-                               nw, lane);
+        consume_tile<MODE, Q4, DEFER>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4, qmask,
+                                      warp, nw, lane, &wm, &cc);
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    flush(w, lane);
+    if (!DEFER) flush(w, lane);  // (a deferred scan flushes its candidates per tile)
 }
 
-template <int MODE, bool Q4, int MAXW>
+template <int MODE, bool Q4, int MAXW, bool DEFER>
 cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                      cudaStream_t st) {
-    auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true>
-                        : rk_scan_tiles_kernel<MODE, Q4, MAXW, false>;
+    auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true, DEFER>
+                        : rk_scan_tiles_kernel<MODE, Q4, MAXW, false, DEFER>;
     // raise the dynamic shared-memory limit once per device and size
     static thread_local int seen_dev[4] = {-1, -1, -1, -1};
     static thread_local uint32_t seen_smem[4] = {0, 0, 0, 0};
@@ -190,27 +199,40 @@ cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint3
     return cudaGetLastError();
 }
 
+template <int MODE, bool Q4, bool DEFER>
+cudaError_t launch_d(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
+                     cudaStream_t st) {
+    if (p.warps <= 8) return launch_w<MODE, Q4, 8, DEFER>(p, grid, threads, smem, st);
+    if (p.warps <= 16) return launch_w<MODE, Q4, 16, DEFER>(p, grid, threads, smem, st);
+    if (p.warps <= 24) return launch_w<MODE, Q4, 24, DEFER>(p, grid, threads, smem, st);
+    return launch_w<MODE, Q4, 31, DEFER>(p, grid, threads, smem, st);
+}
+
 template <int MODE, bool Q4>
 cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                        cudaStream_t st) {
-    if (p.warps <= 8) return launch_w<MODE, Q4, 8>(p, grid, threads, smem, st);
-    if (p.warps <= 16) return launch_w<MODE, Q4, 16>(p, grid, threads, smem, st);
-    if (p.warps <= 24) return launch_w<MODE, Q4, 24>(p, grid, threads, smem, st);
-    return launch_w<MODE, Q4, 31>(p, grid, threads, smem, st);
+    constexpr bool kCanDefer = MODE != kFilterNone;
+    if (kCanDefer && p.cand) return launch_d<MODE, Q4, kCanDefer>(p, grid, threads, smem, st);
+    return launch_d<MODE, Q4, false>(p, grid, threads, smem, st);
 }
 
 }  // namespace
 
 int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
                 uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
-                cudaStream_t stream) {
+                cudaStream_t stream, const CandList *cand) {
     return launch_scan_opts(t, d_text, n, x_begin, x_end, d_keys, capacity, d_info, stream,
-                            kWaitTimeoutNs, false);
+                            kWaitTimeoutNs, false, cand);
+}
+
+bool can_defer(const rk_table *t) {
+    return t->dev.filter_mode != kFilterNone && t->dev.gram_bits <= 64 - kCandSlotShift;
 }
 
 int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
                      uint64_t x_end, uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
-                     cudaStream_t stream, uint64_t timeout_ns, bool withhold) {
+                     cudaStream_t stream, uint64_t timeout_ns, bool withhold,
+                     const CandList *cand) {
     if (x_end > n) x_end = n;
     if (x_begin >= x_end || t->dev.n_patterns == 0) return RK_OK;
     const Tuning &tu = t->tune;
@@ -235,6 +257,11 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     p.s2_smem = tu.s2_smem;
     p.timeout_ns = timeout_ns;
     p.withhold = withhold ? 1u : 0u;
+    if (cand && can_defer(t)) {
+        p.cand = cand->list;
+        p.cand_cap = cand->cap;
+        p.cand_count = cand->count;
+    }
     uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
     uint32_t grid = (uint32_t)(p.n_tiles < max_ctas ? p.n_tiles : max_ctas);
     uint32_t threads = (tu.warps + 1) * 32;

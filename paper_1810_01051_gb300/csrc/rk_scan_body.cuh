@@ -21,30 +21,55 @@ __device__ __forceinline__ uint64_t ld8(const uint8_t *buf, uint32_t pos) {
     return ((uint64_t)hi << 32) | lo;
 }
 
-// Rabin hash of buf[pos .. pos+L) mod 2^61-1 with B = 2^k.
-__device__ __forceinline__ uint64_t window_hash(const uint8_t *buf, uint32_t pos, uint32_t L,
-                                               uint32_t k) {
+__device__ __forceinline__ uint32_t ld1(const uint8_t *buf, uint32_t pos) { return buf[pos]; }
+
+// The text in global memory, for windows read outside a staged tile:
+// positions from a 16-byte aligned base; words at or past `end` (the text
+// end rounded up to 16 bytes) are never read.
+struct GText {
+    const uint8_t *base;
+    uint64_t end;
+};
+
+// As above from global memory.  A word starting at or past `end` holds no
+// text byte; the last word before `end` is read in its place (those bytes
+// lie past the window, and every caller masks or ignores them).
+__device__ __forceinline__ uint64_t ld8(const GText &g, uint64_t pos) {
+    const uint64_t a = pos & ~uint64_t(3), last = g.end - 4;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(g.base);
+    const uint32_t w0 = __ldg(w + (min(a, last) >> 2)), w1 = __ldg(w + (min(a + 4, last) >> 2)),
+                   w2 = __ldg(w + (min(a + 8, last) >> 2));
+    const uint32_t s = (uint32_t)(pos & 3u) * 8u;
+    const uint32_t lo = __funnelshift_r(w0, w1, s), hi = __funnelshift_r(w1, w2, s);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint32_t ld1(const GText &g, uint64_t pos) { return __ldg(g.base + pos); }
+
+// Rabin hash of src[pos .. pos+L) mod 2^61-1 with B = 2^k.
+template <class Src, class Pos>
+__device__ __forceinline__ uint64_t window_hash(const Src &src, Pos pos, uint32_t L, uint32_t k) {
     if (k == 8) {
         // 8-byte blocks: the block's big-endian value, and 256^8 = 2^64 = 2^3 (mod p).
         uint32_t r = ((L - 1u) & 7u) + 1u;  // leading partial block, 1..8 bytes
-        uint64_t h = fold61(bswap64(ld8(buf, pos)) >> (64u - 8u * r));
+        uint64_t h = fold61(bswap64(ld8(src, pos)) >> (64u - 8u * r));
         for (uint32_t i = r; i < L; i += 8)
-            h = addmod61(rotl61(h, 3), fold61(bswap64(ld8(buf, pos + i))));
+            h = addmod61(rotl61(h, 3), fold61(bswap64(ld8(src, pos + i))));
         return h;
     }
     uint64_t h = 0;
     for (uint32_t i = 0; i < L; ++i) {
-        h = rotl61(h, k) + buf[pos + i];
+        h = rotl61(h, k) + ld1(src, pos + i);
         if (h >= kP61) h -= kP61;
     }
     return h;
 }
 
 // pat: 8-byte aligned, zero padded to a multiple of 8 (shared or global).
-__device__ __forceinline__ bool verify(const uint8_t *buf, uint32_t pos, const uint8_t *pat,
-                                       uint32_t L) {
+template <class Src, class Pos>
+__device__ __forceinline__ bool verify(const Src &src, Pos pos, const uint8_t *pat, uint32_t L) {
     for (uint32_t i = 0; i < L; i += 8) {
-        uint64_t d = ld8(buf, pos + i) ^ *reinterpret_cast<const uint64_t *>(pat + i);
+        uint64_t d = ld8(src, pos + i) ^ *reinterpret_cast<const uint64_t *>(pat + i);
         uint32_t rem = L - i;
         if (rem < 8) d &= (1ull << (8u * rem)) - 1ull;
         if (d) return false;
@@ -130,9 +155,9 @@ __device__ __forceinline__ void flush(const WarpCtx &w, uint32_t lane) {
 }
 
 // Probe the length-L group with the window's hash; verify and emit.
-__device__ __forceinline__ void probe_length(const WinCtx &C, const WarpCtx &w,
-                                             const uint8_t *buf, uint32_t pos, uint64_t x,
-                                             uint32_t L) {
+template <class Src, class Pos>
+__device__ __forceinline__ void probe_length(const WinCtx &C, const WarpCtx &w, const Src &buf,
+                                             Pos pos, uint64_t x, uint32_t L) {
     const uint2 hdr = C.s2.group_hdr[L];
     if (hdr.y == 0) return;
     const uint64_t h = window_hash(buf, pos, L, C.base_log2);
@@ -192,6 +217,98 @@ __device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w
     }
 }
 
+// Deferred verification (filtered modes).  Stage 2a below only finds the
+// prefix-map slot whose lengths apply to a window; the candidate (offset |
+// slot << 40) goes to a global list, and a separate kernel hashes, probes
+// and verifies the whole list 32 candidates per warp (rk_verify.cu).
+constexpr uint32_t kCandSlotShift = 40;  // text offsets are below 2^40
+
+// The prefix-map slot whose lengths apply to the window at pos (exact
+// prefix; a length below q + 4, or the next four bytes in the slot's
+// fingerprint set), or -1.
+template <class Src, class Pos>
+__device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos pos) {
+    const uint64_t v = ld8(src, pos);  // window bytes 0..7, little-endian
+    const uint32_t key = C.q == 4 ? (uint32_t)v : (uint32_t)v & ((1u << (8u * C.q)) - 1u);
+    const uint32_t gmask = (1u << C.gram_bits) - 1u;
+    uint32_t idx = (key * kGramMult) >> (32u - C.gram_bits);
+    for (;;) {
+        const GramSlot g = C.s2.grams[idx];
+        if (g.count == 0) return -1;
+        if (g.key == key) {
+            const bool ext_ok = (g.ext >> ext_bit((uint32_t)(v >> (8u * C.q)))) & 1u;
+            return ext_ok || (g.count & kGramShort) ? (int)idx : -1;
+        }
+        idx = (idx + 1) & gmask;
+    }
+}
+
+// Probe every length of prefix-map slot gi that applies to the window at pos
+// (text offset x): A2 hash, A3 probe, A4 verify, A5 emit.
+template <class Src, class Pos>
+__device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, const Src &src,
+                                           Pos pos, uint64_t x, uint32_t gi) {
+    const GramSlot g = C.s2.grams[gi];
+    const bool ext_ok = (g.ext >> ext_bit((uint32_t)(ld8(src, pos) >> (8u * C.q)))) & 1u;
+    const uint32_t cnt = g.count & ~kGramShort;
+    for (uint32_t j = 0; j < cnt; ++j) {
+        const uint32_t L = C.s2.gram_lens[g.first + j];
+        if (x + L > C.n) break;  // lengths ascend
+        if (L >= C.q + 4 && !ext_ok) break;
+        probe_length(C, w, src, pos, x, L);
+    }
+}
+
+// A candidate for which the list has no room is probed at once, with its
+// matches appended straight to the output (wm: a warp context whose buffer
+// counter is saturated, so emit() goes to global memory).
+__device__ __forceinline__ void cand_overflow(const WinCtx &C, const WarpCtx &wm, const uint8_t *buf,
+                                              uint64_t u0, uint64_t e) {
+    const uint64_t x = e & ((1ull << kCandSlotShift) - 1ull);
+    probe_slot(C, wm, buf, (uint32_t)(x + C.mis - u0), x, (uint32_t)(e >> kCandSlotShift));
+}
+
+// Stage 2a for the window at pos of the tile at u0; a candidate is queued in
+// the warp's buffer (w.mbuf), or offered to the list when that is full.
+__device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, const WarpCtx &wm,
+                                            const CandList &cc, const uint8_t *buf, uint32_t pos,
+                                            uint64_t u0) {
+    const uint64_t ua = u0 + pos;
+    if (ua < C.lo || ua >= C.hi) return;
+    const int gi = gram_lookup(C, buf, pos);
+    if (gi < 0) return;
+    const uint64_t e = (ua - C.mis) | ((uint64_t)gi << kCandSlotShift);
+    const uint32_t s = atomicAdd(w.mcount, 1u);
+    if (s < kMatchCap) {
+        w.mbuf[s] = e;
+        return;
+    }
+    const unsigned long long g = atomicAdd(cc.count, 1ull);
+    if (g < cc.cap) cc.list[g] = e;
+    else cand_overflow(C, wm, buf, u0, e);
+}
+
+// Warp-converged: move the buffered candidates to the list with one atomic;
+// those beyond its capacity are probed here (the tile is still staged).
+__device__ __forceinline__ void cand_flush(const WinCtx &C, const WarpCtx &w, const WarpCtx &wm,
+                                           const CandList &cc, const uint8_t *buf, uint64_t u0,
+                                           uint32_t lane) {
+    __syncwarp();
+    const uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kMatchCap);
+    if (cnt) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cc.count, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            if (base + i < cc.cap) cc.list[base + i] = w.mbuf[i];
+            else cand_overflow(C, wm, buf, u0, w.mbuf[i]);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile uint32_t *>(w.mcount) = 0;
+    __syncwarp();
+}
+
 // Stage 1 for one 16-byte chunk, given its words v and the next chunk's first
 // word v4: bit (15 - j) of the result is set when window j may start a match.
 template <int MODE, bool Q4>
@@ -235,12 +352,16 @@ __device__ __forceinline__ Chunk load_chunk(const uint8_t *buf, uint32_t c, uint
 // warp and processed one window per lane, matches flushed at the end.
 //   buf: the tile's shared buffer; u0: its buffer position; nchunks: 16-byte
 //   chunks holding window starts; last: highest chunk index of a full tile.
-template <int MODE, bool Q4>
+// DEFER (filtered modes): survivors only go through stage 2a, candidates to
+// the list of `cc` (w's buffer holds candidates; wm emits overflow matches).
+template <int MODE, bool Q4, bool DEFER = false>
 __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, uint16_t *q,
                                              const uint8_t *buf, uint64_t u0, uint32_t nchunks,
                                              uint32_t last, const uint8_t *sfilt, uint32_t fmask,
                                              uint32_t lane4, uint32_t qmask, uint32_t warp,
-                                             uint32_t nw, uint32_t lane) {
+                                             uint32_t nw, uint32_t lane,
+                                             const WarpCtx *wm = nullptr,
+                                             const CandList *cc = nullptr) {
     uint32_t qn = 0;  // warp-uniform queue length (< 32 between rounds)
     const uint32_t step = nw * 64u;
     uint32_t c0 = warp * 64u;
@@ -276,6 +397,13 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
             // full rounds: one queued window per lane
             while (qn >= 32) {
                 qn -= 32;
+                if (DEFER) {
+                    cand_window(C, w, *wm, *cc, buf, q[qn + lane], u0);
+                    __syncwarp();
+                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32)
+                        cand_flush(C, w, *wm, *cc, buf, u0, lane);
+                    continue;
+                }
                 process_window<MODE>(C, w, buf, q[qn + lane], u0);
                 __syncwarp();
                 if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32)
@@ -287,10 +415,18 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
             while (m) {
                 const uint32_t b = 31u - __clz(m);
                 m &= ~(1u << b);
-                process_window<MODE>(C, w, buf, 16u * (b < 16 ? ca : cb) + (15u - (b & 15u)), u0);
+                const uint32_t pos = 16u * (b < 16 ? ca : cb) + (15u - (b & 15u));
+                if (DEFER) cand_window(C, w, *wm, *cc, buf, pos, u0);
+                else process_window<MODE>(C, w, buf, pos, u0);
             }
-            flush(w, lane);
+            if (DEFER) cand_flush(C, w, *wm, *cc, buf, u0, lane);
+            else flush(w, lane);
         }
+    }
+    if (DEFER) {
+        if (lane < qn) cand_window(C, w, *wm, *cc, buf, q[lane], u0);
+        cand_flush(C, w, *wm, *cc, buf, u0, lane);
+        return;
     }
     if (lane < qn) process_window<MODE>(C, w, buf, q[lane], u0);
     flush(w, lane);

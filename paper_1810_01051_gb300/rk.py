@@ -28,7 +28,7 @@ RK_NOALLOC_MAX_KEYS = 1 << 20
 #: names of every function include/rk.h declares
 EXPORTS = [
     "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
-    "rk_sort_launches",
+    "rk_sort_launches", "rk_scan_workspace_bytes", "rk_scan_device_ws",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
     "rk_window_hashes_device", "rk_search_device_noalloc",
     "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
@@ -119,6 +119,10 @@ def load() -> ctypes.CDLL:
     L.rk_sort_launches.argtypes = [vp, u64, u64, ctypes.POINTER(u32)]
     L.rk_scan_device.restype = ctypes.c_int
     L.rk_scan_device.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+    L.rk_scan_workspace_bytes.restype = u64
+    L.rk_scan_workspace_bytes.argtypes = [vp, u64]
+    L.rk_scan_device_ws.restype = ctypes.c_int
+    L.rk_scan_device_ws.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp]
     L.rk_sort_device.restype = ctypes.c_int
     L.rk_sort_device.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp]
     L.rk_search_device.restype = ctypes.c_int
@@ -242,6 +246,19 @@ def rk_scan_device(table: int, d_text, n: int, d_keys, capacity: int, d_info,
                    stream=None) -> None:
     _check(load().rk_scan_device(table, _ptr(d_text), n, _ptr(d_keys), capacity, _ptr(d_info),
                                  _stream(stream)), "rk_scan_device")
+
+
+def rk_scan_workspace_bytes(table: int, n: int) -> int:
+    """Workspace bytes of rk_scan_device_ws for a text of n bytes."""
+    return int(load().rk_scan_workspace_bytes(table, n))
+
+
+def rk_scan_device_ws(table: int, d_text, n: int, d_keys, capacity: int, d_info, d_workspace,
+                      workspace_bytes: int, stream=None) -> None:
+    """rk_scan_device with the survivors verified by a second kernel."""
+    _check(load().rk_scan_device_ws(table, _ptr(d_text), n, _ptr(d_keys), capacity, _ptr(d_info),
+                                    _ptr(d_workspace), workspace_bytes, _stream(stream)),
+           "rk_scan_device_ws")
 
 
 def rk_sort_device(table: int, n: int, d_keys, capacity: int, d_info, d_workspace,
