@@ -39,7 +39,8 @@ UNIT = "GB/s"
 WORKLOAD = "zipf_text_1GiB_100_patterns_len4-32_density1e-6"
 # the sources the scan kernel is compiled from (the profile records their hash)
 SCAN_SRCS = [os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", f)
-             for f in ("rk_scan.cu", "rk_scan_body.cuh", "rk_layout.cuh", "rk_internal.cuh")]
+             for f in ("rk_scan.cu", "rk_scan_body.cuh", "rk_layout.cuh", "rk_internal.cuh",
+                       "rk_verify.cu", "rk_sortws.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "rk_scan_zipf_1GiB.md")
 CPU_SAMPLE_PER_CORE = 8 << 20   # bytes per core for the oracle baseline
 SLICE_HALO_NOTE = "each slice carries (longest pattern - 1) extra bytes"
@@ -441,22 +442,24 @@ def measure_plain_configs(torch, rk, dev, hbm_gbs, reps=5):
         d = torch.from_numpy(w.text).to(dev)
         table = rk.rk_build(w.patterns)
         cap = 1 << 16
+        scan_b = rk.rk_scan_workspace_bytes(table, w.n)
         while True:
             keys = torch.empty(cap, dtype=torch.int64, device=dev)
             info = torch.zeros(2, dtype=torch.int64, device=dev)
             wsb = rk.rk_workspace_bytes(table, cap)
-            ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-            rk.rk_search_device(table, d, w.n, keys, cap, info, ws, wsb, st)
+            ws = torch.empty(wsb + scan_b, dtype=torch.uint8, device=dev)
+            rk.rk_search_device(table, d, w.n, keys, cap, info, ws, wsb + scan_b, st)
             st.synchronize()
             m = int(info[0])
             if m <= cap:
                 break
             cap = m + 1024
+        sws = ws[wsb:]  # the scan's candidate list after the sort workspace
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         scan_ms, search_ms = [], []
         for _ in range(reps + 1):
             ev[0].record(st)
-            rk.rk_scan_device(table, d, w.n, keys, cap, info, st)
+            rk.rk_scan_device_ws(table, d, w.n, keys, cap, info, sws, scan_b, st)
             ev[1].record(st)
             rk.rk_sort_device(table, w.n, keys, cap, info, ws, wsb, st)
             ev[2].record(st)
@@ -466,6 +469,7 @@ def measure_plain_configs(torch, rk, dev, hbm_gbs, reps=5):
         scan = statistics.median(scan_ms[1:])
         search = statistics.median(search_ms[1:])
         out[name] = {"text_bytes": w.n, "patterns": len(w.patterns), "matches": m,
+                     "scan_kernels": rk.rk_scan_launches(table, w.n, scan_b),
                      "search_ms": search, "gbps": w.n / search / 1e6,
                      "scan_ms": scan, "scan_gbps_algorithmic": (w.n + 8 * m) / scan / 1e6,
                      "scan_frac_of_hbm": (w.n + 8 * m) / scan / 1e6 / hbm_gbs}
@@ -509,13 +513,15 @@ def run_ours(args, rank, world, local_rank):
     st = torch.cuda.Stream(dev)
     d_info = torch.zeros(2, dtype=torch.int64, device=dev)
 
-    # size the output from one probe run
+    # size the output from one probe run; the workspace holds the sort's
+    # scratch and, after it, the deferred scan's candidate list
     cap = 1 << 22
+    scan_b = rk.rk_scan_workspace_bytes(table, n)
     while True:
         keys = torch.empty(cap, dtype=torch.int64, device=dev)
         wsb = rk.rk_workspace_bytes(table, cap)
-        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-        rk.rk_search_device(table, d_text, n, keys, cap, d_info, ws, wsb, st)
+        ws = torch.empty(wsb + scan_b, dtype=torch.uint8, device=dev)
+        rk.rk_search_device(table, d_text, n, keys, cap, d_info, ws, wsb + scan_b, st)
         st.synchronize()
         m, status = (int(v) for v in d_info.cpu().tolist())
         assert status == rk.RK_OK, rk.strerror(status)
@@ -523,12 +529,14 @@ def run_ours(args, rank, world, local_rank):
             break
         cap = m + 1024
 
+    sws = ws[wsb:]
+    scan_kernels = rk.rk_scan_launches(table, n, scan_b)
     sort_kernels = rk.rk_sort_launches(table, n, cap)
 
     def step(evs=None):
         if evs:
             evs[0].record(st)
-        rk.rk_scan_device(table, d_text, n, keys, cap, d_info, st)
+        rk.rk_scan_device_ws(table, d_text, n, keys, cap, d_info, sws, scan_b, st)
         if evs:
             evs[1].record(st)
         rk.rk_sort_device(table, n, keys, cap, d_info, ws, wsb, st)
@@ -638,12 +646,14 @@ def run_ours(args, rank, world, local_rank):
                                              "sm_count")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "scan_kernel", "peak_source": f"{peak_src} hbm_gbs",
+                     "kernel": ("rk_scan_tiles_kernel + rk_verify_kernel (timed together)"
+                                if scan_kernels == 2 else "rk_scan_tiles_kernel"),
+                     "peak_source": f"{peak_src} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": None if args.no_e2e else {
             "value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n,
             "d2h_bytes_per_step": 16 + 8 * m},
-        "gpu_launches": args.steps * (1 + sort_kernels),
+        "gpu_launches": args.steps * (scan_kernels + sort_kernels),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -174,6 +174,13 @@ int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n, uint
                       uint64_t capacity, uint64_t *d_info, void *d_workspace,
                       uint64_t workspace_bytes, void *stream);
 
+/* Kernels rk_scan_device_ws launches for a text of n bytes and a workspace
+ * of workspace_bytes: 2 (tile scan + verification) when it defers, 1 when it
+ * runs rk_scan_device, 0 for an empty text or table (memory clears are not
+ * counted).  Errors: RK_EINVAL (t or launches NULL).                        */
+int rk_scan_launches(const rk_table *t, uint64_t n, uint64_t workspace_bytes,
+                     uint32_t *launches);
+
 /* rk_scan_device followed by rk_sort_device on one stream: the sorted match
  * list of d_text[0..n) in d_keys, its length in d_info[0].  A workspace of
  * rk_workspace_bytes(t, capacity) + rk_scan_workspace_bytes(t, n) bytes

@@ -82,7 +82,7 @@ bool cand_list(const rk_table *t, uint64_t n, void *ws, uint64_t ws_bytes, CandL
     const ScanWsLayout L = scan_ws_layout(n);
     if (!can_defer(t) || !ws || !aligned(ws, 16) || ws_bytes < L.total) return false;
     uint8_t *b = reinterpret_cast<uint8_t *>(ws);
-    *cl = CandList{reinterpret_cast<uint64_t *>(b + L.list_off), L.cap,
+    *cl = CandList{reinterpret_cast<ulonglong2 *>(b + L.list_off), L.cap,
                    reinterpret_cast<unsigned long long *>(b + L.count_off)};
     return true;
 }
@@ -99,6 +99,19 @@ int deferred_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t
 }
 
 }  // namespace
+
+extern "C" int rk_scan_launches(const rk_table *t, uint64_t n, uint64_t workspace_bytes,
+                                uint32_t *launches) {
+    if (!t || !launches) return RK_EINVAL;
+    if (n == 0 || t->dev.n_patterns == 0) {
+        *launches = 0;
+        return RK_OK;
+    }
+    *launches = can_defer(t) && n <= RK_MAX_TEXT_LEN && workspace_bytes >= scan_ws_layout(n).total
+                    ? 2u
+                    : 1u;
+    return RK_OK;
+}
 
 extern "C" int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n,
                                  uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,

@@ -148,9 +148,9 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
 void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dev_base);
 
 // Candidate list of a scan whose survivors are verified in a second pass
-// (entries: text offset | prefix-map slot << 40).
+// (entries: {text offset | prefix-map slot << 40, window bytes 0..7}).
 struct CandList {
-    uint64_t *list;
+    ulonglong2 *list;
     uint64_t cap;
     unsigned long long *count;  // candidates offered (zeroed before the scan; may exceed cap)
 };

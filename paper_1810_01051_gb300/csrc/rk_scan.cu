@@ -53,7 +53,7 @@ struct ScanParams {
     uint64_t timeout_ns;     // limit of every pipeline wait
     uint32_t tile, stages, halo, warps, s2_smem;
     uint32_t withhold;       // diagnostics: the producer issues no copy at all
-    uint64_t *cand;          // deferred verification: candidate list (DEFER kernels)
+    ulonglong2 *cand;        // deferred verification: candidate list (DEFER kernels)
     uint64_t cand_cap;
     unsigned long long *cand_count;
 };

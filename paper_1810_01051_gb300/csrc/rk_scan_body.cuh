@@ -46,6 +46,23 @@ __device__ __forceinline__ uint64_t ld8(const GText &g, uint64_t pos) {
 
 __device__ __forceinline__ uint32_t ld1(const GText &g, uint64_t pos) { return __ldg(g.base + pos); }
 
+// A listed window: its first 8 bytes came with the candidate, anything else
+// is read from the text.
+struct WText {
+    GText g;
+    uint64_t pos0;    // the window's position
+    uint64_t first8;  // bytes pos0 .. pos0 + 7, little-endian
+};
+
+__device__ __forceinline__ uint64_t ld8(const WText &w, uint64_t pos) {
+    return pos == w.pos0 ? w.first8 : ld8(w.g, pos);
+}
+
+__device__ __forceinline__ uint32_t ld1(const WText &w, uint64_t pos) {
+    const uint64_t d = pos - w.pos0;
+    return d < 8 ? (uint32_t)(w.first8 >> (8u * d)) & 0xFFu : ld1(w.g, pos);
+}
+
 // Rabin hash of src[pos .. pos+L) mod 2^61-1 with B = 2^k.
 template <class Src, class Pos>
 __device__ __forceinline__ uint64_t window_hash(const Src &src, Pos pos, uint32_t L, uint32_t k) {
@@ -218,17 +235,21 @@ __device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w
 }
 
 // Deferred verification (filtered modes).  Stage 2a below only finds the
-// prefix-map slot whose lengths apply to a window; the candidate (offset |
-// slot << 40) goes to a global list, and a separate kernel hashes, probes
-// and verifies the whole list 32 candidates per warp (rk_verify.cu).
-constexpr uint32_t kCandSlotShift = 40;  // text offsets are below 2^40
+// prefix-map slot whose lengths apply to a window; the candidate {offset |
+// slot << 40, window bytes 0..7} goes to a global list, and a separate
+// kernel hashes, probes and verifies the whole list 32 candidates per warp
+// (rk_verify.cu), reading longer windows' other bytes from the text.
+constexpr uint32_t kCandSlotShift = 40;          // text offsets are below 2^40
+constexpr uint32_t kCandBuf = kMatchCap / 2;     // 16-byte candidates in a warp's match buffer
 
 // The prefix-map slot whose lengths apply to the window at pos (exact
 // prefix; a length below q + 4, or the next four bytes in the slot's
-// fingerprint set), or -1.
+// fingerprint set), or -1; *v8: the window's bytes 0..7, little-endian.
 template <class Src, class Pos>
-__device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos pos) {
+__device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos pos,
+                                           uint64_t *v8) {
     const uint64_t v = ld8(src, pos);  // window bytes 0..7, little-endian
+    *v8 = v;
     const uint32_t key = C.q == 4 ? (uint32_t)v : (uint32_t)v & ((1u << (8u * C.q)) - 1u);
     const uint32_t gmask = (1u << C.gram_bits) - 1u;
     uint32_t idx = (key * kGramMult) >> (32u - C.gram_bits);
@@ -269,23 +290,25 @@ __device__ __forceinline__ void cand_overflow(const WinCtx &C, const WarpCtx &wm
 }
 
 // Stage 2a for the window at pos of the tile at u0; a candidate is queued in
-// the warp's buffer (w.mbuf), or offered to the list when that is full.
+// the warp's buffer (w.mbuf as kCandBuf 16-byte entries), or offered to the
+// list when that is full.
 __device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, const WarpCtx &wm,
                                             const CandList &cc, const uint8_t *buf, uint32_t pos,
                                             uint64_t u0) {
     const uint64_t ua = u0 + pos;
     if (ua < C.lo || ua >= C.hi) return;
-    const int gi = gram_lookup(C, buf, pos);
+    uint64_t v8;
+    const int gi = gram_lookup(C, buf, pos, &v8);
     if (gi < 0) return;
-    const uint64_t e = (ua - C.mis) | ((uint64_t)gi << kCandSlotShift);
+    const ulonglong2 c = make_ulonglong2((ua - C.mis) | ((uint64_t)gi << kCandSlotShift), v8);
     const uint32_t s = atomicAdd(w.mcount, 1u);
-    if (s < kMatchCap) {
-        w.mbuf[s] = e;
+    if (s < kCandBuf) {
+        reinterpret_cast<ulonglong2 *>(w.mbuf)[s] = c;
         return;
     }
     const unsigned long long g = atomicAdd(cc.count, 1ull);
-    if (g < cc.cap) cc.list[g] = e;
-    else cand_overflow(C, wm, buf, u0, e);
+    if (g < cc.cap) cc.list[g] = c;
+    else cand_overflow(C, wm, buf, u0, c.x);
 }
 
 // Warp-converged: move the buffered candidates to the list with one atomic;
@@ -294,14 +317,15 @@ __device__ __forceinline__ void cand_flush(const WinCtx &C, const WarpCtx &w, co
                                            const CandList &cc, const uint8_t *buf, uint64_t u0,
                                            uint32_t lane) {
     __syncwarp();
-    const uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kMatchCap);
+    const uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kCandBuf);
     if (cnt) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(cc.count, (unsigned long long)cnt);
         base = __shfl_sync(0xffffffffu, base, 0);
+        const ulonglong2 *cb = reinterpret_cast<const ulonglong2 *>(w.mbuf);
         for (uint32_t i = lane; i < cnt; i += 32) {
-            if (base + i < cc.cap) cc.list[base + i] = w.mbuf[i];
-            else cand_overflow(C, wm, buf, u0, w.mbuf[i]);
+            if (base + i < cc.cap) cc.list[base + i] = cb[i];
+            else cand_overflow(C, wm, buf, u0, cb[i].x);
         }
     }
     __syncwarp();
@@ -400,7 +424,7 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
                 if (DEFER) {
                     cand_window(C, w, *wm, *cc, buf, q[qn + lane], u0);
                     __syncwarp();
-                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32)
+                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kCandBuf - 32)
                         cand_flush(C, w, *wm, *cc, buf, u0, lane);
                     continue;
                 }

@@ -36,16 +36,16 @@ __host__ __device__ constexpr uint64_t sort_ws_bytes(uint64_t capacity) {
 
 // Workspace of a scan of n text bytes whose survivors are verified in a
 // second pass: a candidate count and a list of up to n / 64 + 4096
-// candidates (8 bytes each; a scan offered more probes the rest itself).
+// candidates (16 bytes each; a scan offered more probes the rest itself).
 struct ScanWsLayout {
     uint64_t count_off;  // unsigned long long: candidates offered
-    uint64_t list_off;   // uint64_t[cap]
+    uint64_t list_off;   // 16-byte entries [cap]
     uint64_t cap;
     uint64_t total;
 };
 
 __host__ __device__ constexpr ScanWsLayout scan_ws_layout(uint64_t n) {
-    return ScanWsLayout{0, 256, n / 64 + 4096, 256 + ws_align((n / 64 + 4096) * 8)};
+    return ScanWsLayout{0, 256, n / 64 + 4096, 256 + ws_align((n / 64 + 4096) * 16)};
 }
 
 }  // namespace rk

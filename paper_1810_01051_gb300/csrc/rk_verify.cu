@@ -4,8 +4,8 @@
 // fingerprint set).  The scan kernel handles one tile at a time, so its
 // survivor rounds hold only the few candidates of one warp's share of a
 // tile and a warp pays for the longest hash among them; here every warp
-// takes 32 listed candidates at a time and reads their windows from the text
-// in global memory.
+// takes 32 listed candidates at a time; a window's first 8 bytes come with
+// the candidate, longer windows read the rest from the text in global memory.
 #include "rk_scan_body.cuh"
 #include "rk_sortws.cuh"
 
@@ -21,7 +21,7 @@ struct VerifyParams {
     GText text;         // 16-byte aligned base at or before the text start
     uint64_t mis;       // text start - base
     uint64_t n;         // text length
-    const uint64_t *list;
+    const ulonglong2 *list;
     uint64_t cap;
     const unsigned long long *count;
     uint64_t *keys;
@@ -65,9 +65,10 @@ __global__ void __launch_bounds__(kVerifyThreads)
     for (uint64_t i0 = (uint64_t)blockIdx.x * kVerifyThreads + warp * 32; i0 < nc; i0 += stride) {
         const uint64_t i = i0 + lane;
         if (i < nc) {
-            const uint64_t e = P.list[i];
-            const uint64_t x = e & ((1ull << kCandSlotShift) - 1ull);
-            probe_slot(C, w, P.text, x + P.mis, x, (uint32_t)(e >> kCandSlotShift));
+            const ulonglong2 c = P.list[i];
+            const uint64_t x = c.x & ((1ull << kCandSlotShift) - 1ull);
+            const WText win{P.text, x + P.mis, c.y};
+            probe_slot(C, w, win, x + P.mis, x, (uint32_t)(c.x >> kCandSlotShift));
         }
         __syncwarp();
         if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32) flush(w, lane);

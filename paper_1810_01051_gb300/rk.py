@@ -28,7 +28,7 @@ RK_NOALLOC_MAX_KEYS = 1 << 20
 #: names of every function include/rk.h declares
 EXPORTS = [
     "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
-    "rk_sort_launches", "rk_scan_workspace_bytes", "rk_scan_device_ws",
+    "rk_sort_launches", "rk_scan_workspace_bytes", "rk_scan_device_ws", "rk_scan_launches",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
     "rk_window_hashes_device", "rk_search_device_noalloc",
     "rk_tableset_build", "rk_tableset_destroy", "rk_batch_create", "rk_batch_destroy",
@@ -121,6 +121,8 @@ def load() -> ctypes.CDLL:
     L.rk_scan_device.argtypes = [vp, vp, u64, vp, u64, vp, vp]
     L.rk_scan_workspace_bytes.restype = u64
     L.rk_scan_workspace_bytes.argtypes = [vp, u64]
+    L.rk_scan_launches.restype = ctypes.c_int
+    L.rk_scan_launches.argtypes = [vp, u64, u64, ctypes.POINTER(u32)]
     L.rk_scan_device_ws.restype = ctypes.c_int
     L.rk_scan_device_ws.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp]
     L.rk_sort_device.restype = ctypes.c_int
@@ -251,6 +253,15 @@ def rk_scan_device(table: int, d_text, n: int, d_keys, capacity: int, d_info,
 def rk_scan_workspace_bytes(table: int, n: int) -> int:
     """Workspace bytes of rk_scan_device_ws for a text of n bytes."""
     return int(load().rk_scan_workspace_bytes(table, n))
+
+
+def rk_scan_launches(table: int, n: int, workspace_bytes: int) -> int:
+    """Kernels rk_scan_device_ws launches for n text bytes and this workspace."""
+    out = ctypes.c_uint32(0)
+    rc = load().rk_scan_launches(table, n, workspace_bytes, ctypes.byref(out))
+    if rc != RK_OK:
+        raise RuntimeError(f"rk_scan_launches: {strerror(rc)}")
+    return int(out.value)
 
 
 def rk_scan_device_ws(table: int, d_text, n: int, d_keys, capacity: int, d_info, d_workspace,
