@@ -53,9 +53,7 @@ struct ScanParams {
     uint64_t timeout_ns;     // limit of every pipeline wait
     uint32_t tile, stages, halo, warps, s2_smem;
     uint32_t withhold;       // diagnostics: the producer issues no copy at all
-    ulonglong2 *cand;        // deferred verification: candidate list (DEFER kernels)
-    uint64_t cand_cap;
-    unsigned long long *cand_count;
+    CandList cand;           // deferred verification: candidate list (DEFER kernels)
 };
 
 // MAXW: most consumer warps this instance is launched with; the register
@@ -69,7 +67,6 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ volatile uint32_t s_abort;
-    __shared__ uint32_t s_direct[32];  // DEFER: saturated counters, emit() goes to global memory
     const SmemLayout lay =
         smem_layout(P.tab.filter_bytes, P.s2_smem, P.warps, P.stages, P.tile, P.halo);
     uint8_t *sfilt = smem;  // the bit set is first (offset 0): its base folds into addresses
@@ -103,7 +100,6 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         fence_mbar_init();
     }
     if (tid < nw) mcount[tid] = 0;
-    if (DEFER && tid < nw) s_direct[tid] = 0x80000000u;
     __syncthreads();
 
     const uint64_t my_tiles =
@@ -151,8 +147,6 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     C.n_lengths = P.tab.n_lengths;
     uint16_t *q = queues + warp * kQueueCap;
     WarpCtx w{mcount + warp, mbuf + (size_t)warp * kMatchCap, P.keys, P.capacity, P.info};
-    const WarpCtx wm{s_direct + warp, nullptr, P.keys, P.capacity, P.info};
-    const CandList cc{P.cand, P.cand_cap, P.cand_count};
     const uint32_t lane4 = lane << 2;
     const uint32_t fmask = P.tab.filter_mask;
     const uint32_t qmask = P.tab.q == 4 ? 0xFFFFFFFFu : (1u << (8u * P.tab.q)) - 1u;
@@ -171,7 +165,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         const uint64_t wend = min(u0 + P.tile, C.hi);
         const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
         consume_tile<MODE, Q4, DEFER>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4, qmask,
-                                      warp, nw, lane, &wm, &cc);
+                                      warp, nw, lane, &P.cand);
         if (lane == 0) mbar_arrive(&empty[s]);
     }
     if (!DEFER) flush(w, lane);  // (a deferred scan flushes its candidates per tile)
@@ -212,7 +206,7 @@ template <int MODE, bool Q4>
 cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                        cudaStream_t st) {
     constexpr bool kCanDefer = MODE != kFilterNone;
-    if (kCanDefer && p.cand) return launch_d<MODE, Q4, kCanDefer>(p, grid, threads, smem, st);
+    if (kCanDefer && p.cand.list) return launch_d<MODE, Q4, kCanDefer>(p, grid, threads, smem, st);
     return launch_d<MODE, Q4, false>(p, grid, threads, smem, st);
 }
 
@@ -257,11 +251,7 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     p.s2_smem = tu.s2_smem;
     p.timeout_ns = timeout_ns;
     p.withhold = withhold ? 1u : 0u;
-    if (cand && can_defer(t)) {
-        p.cand = cand->list;
-        p.cand_cap = cand->cap;
-        p.cand_count = cand->count;
-    }
+    if (cand && can_defer(t)) p.cand = *cand;
     uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
     uint32_t grid = (uint32_t)(p.n_tiles < max_ctas ? p.n_tiles : max_ctas);
     uint32_t threads = (tu.warps + 1) * 32;

@@ -155,6 +155,12 @@ __device__ __forceinline__ void emit(const WarpCtx &w, uint64_t key) {
     }
 }
 
+// A match appended straight to the output (one global atomic).
+__device__ __forceinline__ void emit_global(const WarpCtx &w, uint64_t key) {
+    const unsigned long long g = atomicAdd(&w.info[0], 1ull);
+    if (g < w.capacity) w.keys[g] = key;
+}
+
 // Warp-converged: move the buffered matches to the output with one atomic.
 __device__ __forceinline__ void flush(const WarpCtx &w, uint32_t lane) {
     __syncwarp();
@@ -171,8 +177,9 @@ __device__ __forceinline__ void flush(const WarpCtx &w, uint32_t lane) {
     __syncwarp();
 }
 
-// Probe the length-L group with the window's hash; verify and emit.
-template <class Src, class Pos>
+// Probe the length-L group with the window's hash; verify and emit (DIRECT:
+// straight to the output, not through the warp's buffer).
+template <bool DIRECT = false, class Src, class Pos>
 __device__ __forceinline__ void probe_length(const WinCtx &C, const WarpCtx &w, const Src &buf,
                                              Pos pos, uint64_t x, uint32_t L) {
     const uint2 hdr = C.s2.group_hdr[L];
@@ -186,8 +193,11 @@ __device__ __forceinline__ void probe_length(const WinCtx &C, const WarpCtx &w, 
         if (s.h == h) {
             for (uint32_t j = 0; j < s.count; ++j) {
                 const uint32_t pid = C.s2.group_pids[s.first + j];
-                if (verify(buf, pos, C.s2.pbytes + C.s2.poff[pid], L))
-                    emit(w, C.key_prefix | ((uint64_t)pid << C.pid_shift) | x);
+                if (verify(buf, pos, C.s2.pbytes + C.s2.poff[pid], L)) {
+                    const uint64_t key = C.key_prefix | ((uint64_t)pid << C.pid_shift) | x;
+                    if (DIRECT) emit_global(w, key);
+                    else emit(w, key);
+                }
             }
             return;
         }
@@ -266,7 +276,7 @@ __device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos 
 
 // Probe every length of prefix-map slot gi that applies to the window at pos
 // (text offset x): A2 hash, A3 probe, A4 verify, A5 emit.
-template <class Src, class Pos>
+template <bool DIRECT = false, class Src, class Pos>
 __device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, const Src &src,
                                            Pos pos, uint64_t x, uint32_t gi) {
     const GramSlot g = C.s2.grams[gi];
@@ -276,25 +286,24 @@ __device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, co
         const uint32_t L = C.s2.gram_lens[g.first + j];
         if (x + L > C.n) break;  // lengths ascend
         if (L >= C.q + 4 && !ext_ok) break;
-        probe_length(C, w, src, pos, x, L);
+        probe_length<DIRECT>(C, w, src, pos, x, L);
     }
 }
 
 // A candidate for which the list has no room is probed at once, with its
-// matches appended straight to the output (wm: a warp context whose buffer
-// counter is saturated, so emit() goes to global memory).
-__device__ __forceinline__ void cand_overflow(const WinCtx &C, const WarpCtx &wm, const uint8_t *buf,
+// matches appended straight to the output (the warp's buffer holds
+// candidates).
+__device__ __forceinline__ void cand_overflow(const WinCtx &C, const WarpCtx &w, const uint8_t *buf,
                                               uint64_t u0, uint64_t e) {
     const uint64_t x = e & ((1ull << kCandSlotShift) - 1ull);
-    probe_slot(C, wm, buf, (uint32_t)(x + C.mis - u0), x, (uint32_t)(e >> kCandSlotShift));
+    probe_slot<true>(C, w, buf, (uint32_t)(x + C.mis - u0), x, (uint32_t)(e >> kCandSlotShift));
 }
 
 // Stage 2a for the window at pos of the tile at u0; a candidate is queued in
 // the warp's buffer (w.mbuf as kCandBuf 16-byte entries), or offered to the
 // list when that is full.
-__device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, const WarpCtx &wm,
-                                            const CandList &cc, const uint8_t *buf, uint32_t pos,
-                                            uint64_t u0) {
+__device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, const CandList &cc,
+                                            const uint8_t *buf, uint32_t pos, uint64_t u0) {
     const uint64_t ua = u0 + pos;
     if (ua < C.lo || ua >= C.hi) return;
     uint64_t v8;
@@ -308,14 +317,13 @@ __device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, c
     }
     const unsigned long long g = atomicAdd(cc.count, 1ull);
     if (g < cc.cap) cc.list[g] = c;
-    else cand_overflow(C, wm, buf, u0, c.x);
+    else cand_overflow(C, w, buf, u0, c.x);
 }
 
 // Warp-converged: move the buffered candidates to the list with one atomic;
 // those beyond its capacity are probed here (the tile is still staged).
-__device__ __forceinline__ void cand_flush(const WinCtx &C, const WarpCtx &w, const WarpCtx &wm,
-                                           const CandList &cc, const uint8_t *buf, uint64_t u0,
-                                           uint32_t lane) {
+__device__ __forceinline__ void cand_flush(const WinCtx &C, const WarpCtx &w, const CandList &cc,
+                                           const uint8_t *buf, uint64_t u0, uint32_t lane) {
     __syncwarp();
     const uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kCandBuf);
     if (cnt) {
@@ -325,7 +333,7 @@ __device__ __forceinline__ void cand_flush(const WinCtx &C, const WarpCtx &w, co
         const ulonglong2 *cb = reinterpret_cast<const ulonglong2 *>(w.mbuf);
         for (uint32_t i = lane; i < cnt; i += 32) {
             if (base + i < cc.cap) cc.list[base + i] = cb[i];
-            else cand_overflow(C, wm, buf, u0, cb[i].x);
+            else cand_overflow(C, w, buf, u0, cb[i].x);
         }
     }
     __syncwarp();
@@ -377,14 +385,13 @@ __device__ __forceinline__ Chunk load_chunk(const uint8_t *buf, uint32_t c, uint
 //   buf: the tile's shared buffer; u0: its buffer position; nchunks: 16-byte
 //   chunks holding window starts; last: highest chunk index of a full tile.
 // DEFER (filtered modes): survivors only go through stage 2a, candidates to
-// the list of `cc` (w's buffer holds candidates; wm emits overflow matches).
+// the list `cc` (w's buffer then holds candidates).
 template <int MODE, bool Q4, bool DEFER = false>
 __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, uint16_t *q,
                                              const uint8_t *buf, uint64_t u0, uint32_t nchunks,
                                              uint32_t last, const uint8_t *sfilt, uint32_t fmask,
                                              uint32_t lane4, uint32_t qmask, uint32_t warp,
                                              uint32_t nw, uint32_t lane,
-                                             const WarpCtx *wm = nullptr,
                                              const CandList *cc = nullptr) {
     uint32_t qn = 0;  // warp-uniform queue length (< 32 between rounds)
     const uint32_t step = nw * 64u;
@@ -422,10 +429,10 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
             while (qn >= 32) {
                 qn -= 32;
                 if (DEFER) {
-                    cand_window(C, w, *wm, *cc, buf, q[qn + lane], u0);
+                    cand_window(C, w, *cc, buf, q[qn + lane], u0);
                     __syncwarp();
                     if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kCandBuf - 32)
-                        cand_flush(C, w, *wm, *cc, buf, u0, lane);
+                        cand_flush(C, w, *cc, buf, u0, lane);
                     continue;
                 }
                 process_window<MODE>(C, w, buf, q[qn + lane], u0);
@@ -440,16 +447,16 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
                 const uint32_t b = 31u - __clz(m);
                 m &= ~(1u << b);
                 const uint32_t pos = 16u * (b < 16 ? ca : cb) + (15u - (b & 15u));
-                if (DEFER) cand_window(C, w, *wm, *cc, buf, pos, u0);
+                if (DEFER) cand_window(C, w, *cc, buf, pos, u0);
                 else process_window<MODE>(C, w, buf, pos, u0);
             }
-            if (DEFER) cand_flush(C, w, *wm, *cc, buf, u0, lane);
+            if (DEFER) cand_flush(C, w, *cc, buf, u0, lane);
             else flush(w, lane);
         }
     }
     if (DEFER) {
-        if (lane < qn) cand_window(C, w, *wm, *cc, buf, q[lane], u0);
-        cand_flush(C, w, *wm, *cc, buf, u0, lane);
+        if (lane < qn) cand_window(C, w, *cc, buf, q[lane], u0);
+        cand_flush(C, w, *cc, buf, u0, lane);
         return;
     }
     if (lane < qn) process_window<MODE>(C, w, buf, q[lane], u0);
