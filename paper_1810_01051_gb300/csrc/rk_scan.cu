@@ -31,6 +31,8 @@
 // All waits are bounded; on a timeout the kernel records RK_ETIMEOUT in
 // d_info[1], stops issuing copies, waits (bounded) for its copies in flight
 // and returns.
+#include <algorithm>
+
 #include "rk_scan_body.cuh"
 
 namespace rk {
@@ -240,11 +242,21 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     p.x_end = x_end;
     p.u_first = (p.mis + x_begin) & ~uint64_t(15);
     p.n16 = (p.mis + n + 15) & ~uint64_t(15);
-    p.n_tiles = (p.mis + x_end - p.u_first + tu.tile_bytes - 1) / tu.tile_bytes;
+    // A text shorter than one tile per CTA takes smaller tiles (whole
+    // stage-1 rounds of every warp, warps x 1 KiB) so that every SM works;
+    // they fit the shared memory sized for the table's tile.
+    const uint64_t span = p.mis + x_end - p.u_first;
+    const uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
+    const uint64_t round_bytes = (uint64_t)tu.warps * 1024u;
+    const uint64_t per_cta = (span + max_ctas - 1) / max_ctas;
+    const uint32_t tile = (uint32_t)std::min<uint64_t>(
+        tu.tile_bytes, std::max<uint64_t>(round_bytes, (per_cta + round_bytes - 1) / round_bytes *
+                                                           round_bytes));
+    p.n_tiles = (span + tile - 1) / tile;
     p.keys = d_keys;
     p.capacity = capacity;
     p.info = reinterpret_cast<unsigned long long *>(d_info);
-    p.tile = tu.tile_bytes;
+    p.tile = tile;
     p.stages = tu.stages;
     p.halo = tu.halo;
     p.warps = tu.warps;
@@ -252,7 +264,6 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     p.timeout_ns = timeout_ns;
     p.withhold = withhold ? 1u : 0u;
     if (cand && can_defer(t)) p.cand = *cand;
-    uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
     uint32_t grid = (uint32_t)(p.n_tiles < max_ctas ? p.n_tiles : max_ctas);
     uint32_t threads = (tu.warps + 1) * 32;
     bool q4 = t->dev.q == 4;
