@@ -82,6 +82,10 @@ typedef struct rk_build_opts {
                                   (default 49152) */
     uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */
     uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
+    uint32_t sample;           /* 0: when every pattern has >= 7 bytes, scans with a candidate
+                                  list (rk_scan_device_ws) test every 4th window position
+                                  against the patterns' 4-byte grams at offsets 0..3;
+                                  1: every position against the prefixes */
 } rk_build_opts;
 
 /* Read-back of a table's shape and launch configuration. */
@@ -96,6 +100,8 @@ typedef struct rk_table_info {
     uint32_t device;
     uint32_t s2_smem_bytes;    /* survivor-stage tables staged in shared memory (0: read from L2) */
     uint64_t device_bytes;     /* device memory held by the table */
+    uint32_t sample_step;      /* 4: sampled stage 1 available (see rk_build_opts.sample), else 1 */
+    uint32_t sample_filter_log2_bits;  /* its bit set's size (0 without) */
 } rk_table_info;
 
 /* Human-readable text of a status code (static storage). */

@@ -348,7 +348,7 @@ extern "C" int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, con
         const uint32_t k = patterns_per_table[i];
         if (k > RK_MAX_PATTERNS) { delete ts; return RK_EINVAL; }
         int rc = build_blob(patterns + byte_off, lens + pat_off, k, base_log2, filt,
-                            o.filter_log2_bits, &blobs[i]);
+                            o.filter_log2_bits, 1, &blobs[i]);  // table sets are scanned unsampled
         if (rc) { delete ts; return rc; }
         for (uint32_t j = 0; j < k; ++j) byte_off += lens[pat_off + j];
         pat_off += k;

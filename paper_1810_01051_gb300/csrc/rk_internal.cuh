@@ -42,6 +42,13 @@ struct GramSlot {
 };
 constexpr uint32_t kGramShort = 1u << 31;
 
+// One slot of the sample map: a 4-byte gram (little-endian) and the set of
+// offsets j (bit j, j < 4) at which it starts in some pattern; mask 0 = empty.
+struct SampSlot {
+    uint32_t key;
+    uint32_t mask;
+};
+
 // Bit of `ext` for four bytes read as a little-endian word.
 __host__ __device__ __forceinline__ uint32_t ext_bit(uint32_t w) {
     return (w * 0x9E3779B1u) >> 27;
@@ -69,6 +76,17 @@ struct DevTable {
     const uint32_t *plen;
     const uint32_t *lengths;  // distinct lengths, ascending
     uint32_t n_lengths;
+
+    // Sampled stage 1 (sample == 4): every pattern has at least 7 bytes, so a
+    // window starting at x has its position p = x + j (j < 4, p = 0 mod 4)
+    // inside the pattern's first 7 bytes; stage 1 then tests only positions
+    // p = 0 mod 4 against the patterns' 4-byte grams at offsets 0..3, and the
+    // sample map gives each gram's offsets.
+    uint32_t sample;          // 4, or 1: no sampled structures
+    const uint32_t *sfilter;  // bit set of the grams (same layouts as `filter`)
+    uint32_t sfilter_bytes, sfilter_mode, sfilter_mask;
+    const SampSlot *smap;     // 2^smap_bits slots (in the survivor-stage tables)
+    uint32_t smap_bits;
 
     uint32_t n_patterns;
     uint32_t lmin, lmax;
@@ -101,6 +119,7 @@ struct rk_table {
     rk::Tuning tune{};
     uint32_t n_grams = 0;
     uint32_t filter_log2_bits = 0;
+    uint32_t sfilter_log2_bits = 0;
     uint32_t filter_opt = RK_FILTER_AUTO;
     void *d_mem = nullptr;
     size_t d_bytes = 0;
@@ -138,13 +157,15 @@ namespace rk {
 struct TableBlob {
     std::vector<uint8_t> bytes;
     size_t o_filter = 0, o_grams = 0, o_glens = 0, o_ghdr = 0, o_slots = 0, o_gpids = 0,
-           o_pbytes = 0, o_poff = 0, o_plen = 0, o_lens = 0;
+           o_pbytes = 0, o_poff = 0, o_plen = 0, o_lens = 0, o_sfilter = 0, o_smap = 0;
     DevTable meta{};
-    uint32_t n_grams = 0, filter_log2_bits = 0;
+    uint32_t n_grams = 0, filter_log2_bits = 0, sfilter_log2_bits = 0;
 };
 
+// sample_opt: rk_build_opts.sample (1: no sampled structures).
 int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
-               uint32_t filter_opt, uint32_t filter_bits_opt, TableBlob *out);
+               uint32_t filter_opt, uint32_t filter_bits_opt, uint32_t sample_opt,
+               TableBlob *out);
 void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dev_base);
 
 // Candidate list of a scan whose survivors are verified in a second pass

@@ -64,7 +64,9 @@ struct ScanParams {
 // compile to shared-memory loads).  DEFER: survivors stop after the
 // prefix-map stage and go to the candidate list (verified by
 // rk_verify_kernel).
-template <int MODE, bool Q4, int MAXW, bool S2S, bool DEFER>
+// SAMP (DEFER, q = 4): stage 1 tests every 4th position against the bit set
+// of the patterns' grams at offsets 0..3 (P.tab.filter is that bit set).
+template <int MODE, bool Q4, int MAXW, bool S2S, bool DEFER, bool SAMP>
 __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     C.gram_bits = P.tab.gram_bits;
     C.base_log2 = P.tab.base_log2;
     C.n_lengths = P.tab.n_lengths;
+    C.smap_bits = P.tab.smap_bits;
     uint16_t *q = queues + warp * kQueueCap;
     WarpCtx w{mcount + warp, mbuf + (size_t)warp * kMatchCap, P.keys, P.capacity, P.info};
     const uint32_t lane4 = lane << 2;
@@ -166,18 +169,22 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         const uint64_t u0 = P.u_first + t * P.tile;
         const uint64_t wend = min(u0 + P.tile, C.hi);
         const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
-        consume_tile<MODE, Q4, DEFER>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4, qmask,
-                                      warp, nw, lane, &P.cand);
+        if (SAMP)
+            consume_tile_s4<MODE>(C, w, q, buf, u0, nchunks, P.tile, sfilt, fmask, lane4, warp, nw,
+                                  lane, P.cand);
+        else
+            consume_tile<MODE, Q4, DEFER>(C, w, q, buf, u0, nchunks, last, sfilt, fmask, lane4,
+                                          qmask, warp, nw, lane, &P.cand);
         if (lane == 0) mbar_arrive(&empty[s]);
     }
     if (!DEFER) flush(w, lane);  // (a deferred scan flushes its candidates per tile)
 }
 
-template <int MODE, bool Q4, int MAXW, bool DEFER>
+template <int MODE, bool Q4, int MAXW, bool DEFER, bool SAMP>
 cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                      cudaStream_t st) {
-    auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true, DEFER>
-                        : rk_scan_tiles_kernel<MODE, Q4, MAXW, false, DEFER>;
+    auto fn = p.s2_smem ? rk_scan_tiles_kernel<MODE, Q4, MAXW, true, DEFER, SAMP>
+                        : rk_scan_tiles_kernel<MODE, Q4, MAXW, false, DEFER, SAMP>;
     // raise the dynamic shared-memory limit once per device and size
     static thread_local int seen_dev[4] = {-1, -1, -1, -1};
     static thread_local uint32_t seen_smem[4] = {0, 0, 0, 0};
@@ -195,21 +202,25 @@ cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint3
     return cudaGetLastError();
 }
 
-template <int MODE, bool Q4, bool DEFER>
+template <int MODE, bool Q4, bool DEFER, bool SAMP>
 cudaError_t launch_d(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                      cudaStream_t st) {
-    if (p.warps <= 8) return launch_w<MODE, Q4, 8, DEFER>(p, grid, threads, smem, st);
-    if (p.warps <= 16) return launch_w<MODE, Q4, 16, DEFER>(p, grid, threads, smem, st);
-    if (p.warps <= 24) return launch_w<MODE, Q4, 24, DEFER>(p, grid, threads, smem, st);
-    return launch_w<MODE, Q4, 31, DEFER>(p, grid, threads, smem, st);
+    if (p.warps <= 8) return launch_w<MODE, Q4, 8, DEFER, SAMP>(p, grid, threads, smem, st);
+    if (p.warps <= 16) return launch_w<MODE, Q4, 16, DEFER, SAMP>(p, grid, threads, smem, st);
+    if (p.warps <= 24) return launch_w<MODE, Q4, 24, DEFER, SAMP>(p, grid, threads, smem, st);
+    return launch_w<MODE, Q4, 31, DEFER, SAMP>(p, grid, threads, smem, st);
 }
 
 template <int MODE, bool Q4>
 cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool samp) {
     constexpr bool kCanDefer = MODE != kFilterNone;
-    if (kCanDefer && p.cand.list) return launch_d<MODE, Q4, kCanDefer>(p, grid, threads, smem, st);
-    return launch_d<MODE, Q4, false>(p, grid, threads, smem, st);
+    constexpr bool kCanSample = kCanDefer && Q4;
+    if (kCanSample && p.cand.list && samp)
+        return launch_d<MODE, Q4, kCanDefer, kCanSample>(p, grid, threads, smem, st);
+    if (kCanDefer && p.cand.list)
+        return launch_d<MODE, Q4, kCanDefer, false>(p, grid, threads, smem, st);
+    return launch_d<MODE, Q4, false, false>(p, grid, threads, smem, st);
 }
 
 }  // namespace
@@ -264,22 +275,31 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     p.timeout_ns = timeout_ns;
     p.withhold = withhold ? 1u : 0u;
     if (cand && can_defer(t)) p.cand = *cand;
+    // a deferred scan of a sampled table stages the grams' bit set instead
+    const bool samp = p.cand.list && t->dev.sample == 4;
+    if (samp) {
+        p.tab.filter = t->dev.sfilter;
+        p.tab.filter_bytes = t->dev.sfilter_bytes;
+        p.tab.filter_mode = t->dev.sfilter_mode;
+        p.tab.filter_mask = t->dev.sfilter_mask;
+    }
     uint32_t grid = (uint32_t)(p.n_tiles < max_ctas ? p.n_tiles : max_ctas);
     uint32_t threads = (tu.warps + 1) * 32;
     bool q4 = t->dev.q == 4;
+    const uint32_t sm = tu.smem_bytes;
     cudaError_t e;
-    switch (t->dev.filter_mode) {
+    switch (p.tab.filter_mode) {
         case kFilterNone:
-            e = q4 ? launch_one<kFilterNone, true>(p, grid, threads, tu.smem_bytes, stream)
-                   : launch_one<kFilterNone, false>(p, grid, threads, tu.smem_bytes, stream);
+            e = q4 ? launch_one<kFilterNone, true>(p, grid, threads, sm, stream, samp)
+                   : launch_one<kFilterNone, false>(p, grid, threads, sm, stream, samp);
             break;
         case kFilterReplicated:
-            e = q4 ? launch_one<kFilterReplicated, true>(p, grid, threads, tu.smem_bytes, stream)
-                   : launch_one<kFilterReplicated, false>(p, grid, threads, tu.smem_bytes, stream);
+            e = q4 ? launch_one<kFilterReplicated, true>(p, grid, threads, sm, stream, samp)
+                   : launch_one<kFilterReplicated, false>(p, grid, threads, sm, stream, samp);
             break;
         default:
-            e = q4 ? launch_one<kFilterFlat, true>(p, grid, threads, tu.smem_bytes, stream)
-                   : launch_one<kFilterFlat, false>(p, grid, threads, tu.smem_bytes, stream);
+            e = q4 ? launch_one<kFilterFlat, true>(p, grid, threads, sm, stream, samp)
+                   : launch_one<kFilterFlat, false>(p, grid, threads, sm, stream, samp);
             break;
     }
     return e == cudaSuccess ? RK_OK : RK_ECUDA;

@@ -104,6 +104,7 @@ struct S2 {
     const uint8_t *pbytes;
     const uint64_t *poff;
     const uint32_t *lengths;
+    const SampSlot *smap;  // sampled tables only
 };
 
 template <class T>
@@ -123,6 +124,7 @@ __device__ __forceinline__ S2 make_s2(const DevTable &T, const uint8_t *to) {
     s.pbytes = rebase(T.pbytes, from, to);
     s.poff = rebase(T.poff, from, to);
     s.lengths = rebase(T.lengths, from, to);
+    s.smap = rebase(T.smap, from, to);
     return s;
 }
 
@@ -135,6 +137,7 @@ struct WinCtx {
     uint64_t key_prefix;  // or-ed into every key
     uint32_t pid_shift;   // bit position of the pattern id in a key
     uint32_t q, gram_bits, base_log2, n_lengths;
+    uint32_t smap_bits;   // sampled tables: sample map size (log2 slots)
 };
 
 struct WarpCtx {
@@ -461,6 +464,126 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
     }
     if (lane < qn) process_window<MODE>(C, w, buf, q[lane], u0);
     flush(w, lane);
+}
+
+// ------------------------------------------------------------ sampled scan
+// Stage 1 over sampled positions only (tables with sample == 4, deferred
+// scans): bit i of the result is set when the word at position 4i of the
+// 16-byte chunk may be the gram at offset j < 4 of some pattern.  The flat
+// bit set of the grams has two bits per gram in one word (the second from
+// the hash's top 5 bits): both must be set.
+template <int MODE>
+__device__ __forceinline__ uint32_t stage1_s4(const uint4 v, const uint8_t *sfilt, uint32_t fmask,
+                                              uint32_t lane4) {
+    const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        const uint32_t hh = __umulhi(wd[i], kFilterMult);
+        const uint32_t a = MODE == kFilterReplicated ? ((hh & fmask) | lane4) : ((hh >> 3) & fmask);
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(sfilt + a);
+        uint32_t rot = __funnelshift_r(word, word, hh);  // bucket bit -> bit 31
+        if (MODE == kFilterFlat) rot &= __funnelshift_r(word, word, hh >> 27);
+        acc = __funnelshift_l(rot, acc, 1);  // word i ends in bit i
+    }
+    return acc;
+}
+
+// A sampled position pos (a multiple of 4) that passed stage 1: each offset
+// j of its gram in the sample map gives the window pos - j, which is offered
+// to stage 2a when it belongs to this tile (windows before the tile were
+// offered by the previous tile, whose last sampled position is this tile's
+// first).
+__device__ __forceinline__ void samp_window(const WinCtx &C, const WarpCtx &w, const CandList &cc,
+                                            const uint8_t *buf, uint32_t pos, uint64_t u0,
+                                            uint32_t tile) {
+    const uint32_t key = *reinterpret_cast<const uint32_t *>(buf + pos);
+    const uint32_t smask = (1u << C.smap_bits) - 1u;
+    uint32_t idx = (key * kGramMult) >> (32u - C.smap_bits);
+    uint32_t offs = 0;
+    for (;;) {
+        const SampSlot e = C.s2.smap[idx];
+        if (e.mask == 0) return;  // a false positive of the bit set
+        if (e.key == key) {
+            offs = e.mask;
+            break;
+        }
+        idx = (idx + 1) & smask;
+    }
+    for (uint32_t j = 0; j < 4; ++j)
+        if (((offs >> j) & 1u) && pos >= j && pos - j < tile) cand_window(C, w, cc, buf, pos - j, u0);
+}
+
+// One consumer warp's share of a staged tile in a sampled, deferred scan:
+// chunks warp*128 + lane + 32k (k < 4) + r * nw * 128, four sampled
+// positions per chunk (16 per lane per round), the positions that pass
+// queued and handled one per lane.  Chunk nchunks (the next tile's first,
+// in the halo) is tested too: its words start the windows at the tile's end.
+template <int MODE>
+__device__ __forceinline__ void consume_tile_s4(const WinCtx &C, const WarpCtx &w, uint16_t *q,
+                                                const uint8_t *buf, uint64_t u0, uint32_t nchunks,
+                                                uint32_t tile, const uint8_t *sfilt,
+                                                uint32_t fmask, uint32_t lane4, uint32_t warp,
+                                                uint32_t nw, uint32_t lane, const CandList &cc) {
+    const uint32_t nch = nchunks + 1, lastc = tile / 16u;  // chunk tile/16 lies in the halo
+    uint32_t qn = 0;  // warp-uniform queue length (< 32 between rounds)
+    const uint32_t step = nw * 128u;
+    uint32_t c0 = warp * 128u;
+    uint4 k[4];
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i)
+        k[i] = *reinterpret_cast<const uint4 *>(buf + 16u * min(c0 + lane + 32u * i, lastc));
+    while (c0 < nch) {
+        uint4 nk[4];
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i)
+            nk[i] = *reinterpret_cast<const uint4 *>(buf + 16u * min(c0 + step + lane + 32u * i, lastc));
+        uint32_t m = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i)
+            if (c0 + lane + 32u * i < nch) m |= stage1_s4<MODE>(k[i], sfilt, fmask, lane4) << (4u * i);
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i) k[i] = nk[i];
+        const uint32_t cbase = c0 + lane;
+        c0 += step;
+        if (__ballot_sync(0xffffffffu, m != 0) == 0) continue;
+        // bit b of m: word b & 3 of chunk cbase + 32 * (b >> 2)
+        const uint32_t cnt = __popc(m);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (qn + total <= kQueueCap) {
+            uint32_t at = qn + incl - cnt;
+            while (m) {
+                const uint32_t b = 31u - __clz(m);
+                m &= ~(1u << b);
+                q[at++] = (uint16_t)(16u * (cbase + 32u * (b >> 2)) + 4u * (b & 3u));
+            }
+            qn += total;
+            __syncwarp();
+            while (qn >= 32) {  // full rounds: one queued position per lane
+                qn -= 32;
+                samp_window(C, w, cc, buf, q[qn + lane], u0, tile);
+                __syncwarp();
+                if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kCandBuf - 32)
+                    cand_flush(C, w, cc, buf, u0, lane);
+            }
+        } else {
+            while (m) {  // more than the queue holds: each lane works through its own
+                const uint32_t b = 31u - __clz(m);
+                m &= ~(1u << b);
+                samp_window(C, w, cc, buf, 16u * (cbase + 32u * (b >> 2)) + 4u * (b & 3u), u0,
+                            tile);
+            }
+            cand_flush(C, w, cc, buf, u0, lane);
+        }
+    }
+    if (lane < qn) samp_window(C, w, cc, buf, q[lane], u0, tile);
+    cand_flush(C, w, cc, buf, u0, lane);
 }
 
 }  // namespace rk

@@ -84,10 +84,66 @@ extern "C" const char *rk_strerror(int status) {
 
 namespace rk {
 
+namespace {
+
+// Stage-1 bit set of `keys` (4-byte little-endian values or q-byte prefixes):
+// the layout (replicated into 32 banks or flat), its size and the device
+// image.  Returns false for an invalid forced size.
+// two_bits (flat layout): each key sets a second bit of the same word, taken
+// from the hash's top 5 bits, and a key passes only when both are set.
+bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_t bits_opt,
+                 bool two_bits, uint32_t *mode, uint32_t *fbits, std::vector<uint32_t> *img,
+                 uint32_t *fmask) {
+    const uint64_t D = keys.size();
+    *fbits = bits_opt;
+    if (filter_opt == RK_FILTER_NONE) {
+        *mode = kFilterNone;
+    } else if (filter_opt == RK_FILTER_REPLICATED ||
+               (filter_opt == RK_FILTER_AUTO && D <= 256 && !bits_opt)) {
+        *mode = kFilterReplicated;
+        if (!*fbits) *fbits = 14;
+        if (*fbits < 10 || *fbits > 15) return false;
+    } else {
+        *mode = kFilterFlat;
+        // about 1 in 32 bits set (two bits per key: at most 2^19 bits, 64 KiB,
+        // so that two 48 KiB tiles still fit beside it)
+        if (!*fbits)
+            *fbits = std::min<uint32_t>(two_bits ? 19 : 20,
+                                        std::max<uint32_t>(15, ceil_log2(32ull * D)));
+        if (*fbits < 10 || *fbits > 20) return false;
+    }
+    img->clear();
+    *fmask = 0;
+    if (*mode == kFilterNone) return true;
+    const uint32_t W = 1u << (*fbits - 5);
+    std::vector<uint32_t> bm(W, 0);
+    for (uint32_t key : keys) {
+        const uint32_t hi = (uint32_t)(((uint64_t)key * kFilterMult) >> 32);
+        const uint32_t word = (*mode == kFilterReplicated ? (hi >> 7) : (hi >> 5)) & (W - 1);
+        const uint32_t r = hi & 31;
+        // stored one place below r: a right rotation by r moves it to bit 31
+        bm[word] |= 1u << ((r + 31) & 31);
+        if (two_bits && *mode == kFilterFlat) bm[word] |= 1u << (((hi >> 27) + 31) & 31);
+    }
+    if (*mode == kFilterReplicated) {
+        img->resize((size_t)W * 32);
+        for (uint32_t w = 0; w < W; ++w)
+            for (uint32_t l = 0; l < 32; ++l) (*img)[(size_t)w * 32 + l] = bm[w];
+        *fmask = (W - 1) << 7;
+    } else {
+        *img = bm;
+        *fmask = (W - 1) << 2;
+    }
+    return true;
+}
+
+}  // namespace
+
 // Serialise the pattern table of one pattern set into a host image; every
 // part is 256-byte aligned and the image ends on a 256-byte boundary.
 int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
-               uint32_t filter_opt, uint32_t filter_bits_opt, TableBlob *out) {
+               uint32_t filter_opt, uint32_t filter_bits_opt, uint32_t sample_opt,
+               TableBlob *out) {
     // ---- patterns ---------------------------------------------------------
     std::vector<uint64_t> src_off(k), poff(k);
     std::vector<uint32_t> plen(k);
@@ -147,40 +203,39 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     }
 
     // ---- stage-1 bit set ---------------------------------------------------
-    uint32_t mode, fbits = filter_bits_opt;
-    if (filter_opt == RK_FILTER_NONE) {
-        mode = kFilterNone;
-    } else if (filter_opt == RK_FILTER_REPLICATED ||
-               (filter_opt == RK_FILTER_AUTO && D <= 256 && !fbits)) {
-        mode = kFilterReplicated;
-        if (!fbits) fbits = 14;
-        if (fbits < 10 || fbits > 15) return RK_EINVAL;
-    } else {
-        mode = kFilterFlat;
-        if (!fbits) fbits = std::min<uint32_t>(20, std::max<uint32_t>(15, ceil_log2(64ull * D)));
-        if (fbits < 10 || fbits > 20) return RK_EINVAL;
-    }
+    uint32_t mode, fbits, fmask;
     std::vector<uint32_t> fimg;
-    uint32_t fmask = 0;
-    if (mode != kFilterNone) {
-        uint32_t W = 1u << (fbits - 5);
-        std::vector<uint32_t> bm(W, 0);
-        for (uint32_t key : gram_keys) {
-            uint32_t hi = (uint32_t)(((uint64_t)key * kFilterMult) >> 32);
-            uint32_t word = (mode == kFilterReplicated ? (hi >> 7) : (hi >> 5)) & (W - 1);
-            uint32_t r = hi & 31;
-            // stored one place below r: a right rotation by r moves it to bit 31
-            bm[word] |= 1u << ((r + 31) & 31);
+    if (!make_filter(gram_keys, filter_opt, filter_bits_opt, false, &mode, &fbits, &fimg, &fmask))
+        return RK_EINVAL;
+
+    // ---- sampled stage 1: 4-byte grams at offsets 0..3, their offset sets --
+    const bool sampled = sample_opt != 1 && mode != kFilterNone && q == 4 && lmin >= 7;
+    std::vector<SampSlot> smap;
+    std::vector<uint32_t> simg;
+    uint32_t smap_bits = 0, smode = 0, sbits = 0, smask_addr = 0;
+    if (sampled) {
+        std::unordered_map<uint32_t, uint32_t> offs;
+        offs.reserve(k * 8 + 1);
+        for (uint32_t i = 0; i < k; ++i)
+            for (uint32_t j = 0; j < 4; ++j)
+                offs[prefix_key(patterns + src_off[i] + j, 4)] |= 1u << j;
+        std::vector<uint32_t> skeys;
+        skeys.reserve(offs.size());
+        for (auto &kv : offs) skeys.push_back(kv.first);
+        std::sort(skeys.begin(), skeys.end());
+        smap_bits = std::max<uint32_t>(4, ceil_log2(2ull * skeys.size()));
+        smap.assign(1ull << smap_bits, SampSlot{0, 0});
+        const uint32_t smask = (1u << smap_bits) - 1;
+        for (uint32_t key : skeys) {
+            uint32_t idx = (key * kGramMult) >> (32 - smap_bits);
+            while (smap[idx].mask) idx = (idx + 1) & smask;
+            smap[idx] = SampSlot{key, offs[key]};
         }
-        if (mode == kFilterReplicated) {
-            fimg.resize((size_t)W * 32);
-            for (uint32_t w = 0; w < W; ++w)
-                for (uint32_t l = 0; l < 32; ++l) fimg[(size_t)w * 32 + l] = bm[w];
-            fmask = (W - 1) << 7;
-        } else {
-            fimg = bm;
-            fmask = (W - 1) << 2;
-        }
+        // the same layout choice as the prefix bit set, for this key set; a
+        // flat one tests two bits per gram (stage 1 tests 4x fewer positions)
+        if (!make_filter(skeys, filter_opt, filter_bits_opt, true, &smode, &sbits, &simg,
+                         &smask_addr))
+            return RK_EINVAL;
     }
 
     // ---- per-length hash tables -------------------------------------------
@@ -230,6 +285,8 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     size_t o_poff = b.add(k * 8 + 8);
     size_t o_plen = b.add(k * 4 + 4);
     size_t o_lens = b.add(lengths.size() * 4 + 4);
+    size_t o_smap = b.add(smap.size() * sizeof(SampSlot) + 8);
+    size_t o_sfilter = b.add(simg.size() * 4 + 16);  // after the survivor tables: not staged with them
     b.add(0);  // the blob ends on a 256-byte boundary: whole 16-byte copies stay inside
     uint8_t *hb = b.bytes.data();
     if (!fimg.empty()) memcpy(hb + o_filter, fimg.data(), fimg.size() * 4);
@@ -242,6 +299,8 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     if (k) memcpy(hb + o_poff, poff.data(), k * 8);
     if (k) memcpy(hb + o_plen, plen.data(), k * 4);
     if (!lengths.empty()) memcpy(hb + o_lens, lengths.data(), lengths.size() * 4);
+    if (!smap.empty()) memcpy(hb + o_smap, smap.data(), smap.size() * sizeof(SampSlot));
+    if (!simg.empty()) memcpy(hb + o_sfilter, simg.data(), simg.size() * 4);
 
     if (b.bytes.size() - o_grams > 0xFFFFFFFFull) return RK_EINVAL;  // tables above 4 GiB
     TableBlob &tb = *out;
@@ -255,6 +314,8 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     tb.o_poff = o_poff;
     tb.o_plen = o_plen;
     tb.o_lens = o_lens;
+    tb.o_smap = o_smap;
+    tb.o_sfilter = o_sfilter;
     DevTable &d = tb.meta;
     d = DevTable{};
     d.filter_bytes = (uint32_t)(fimg.size() * 4);
@@ -267,9 +328,15 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     d.lmin = lmin;
     d.lmax = lmax;
     d.base_log2 = base_log2;
-    d.s2_bytes = (uint32_t)(b.bytes.size() - o_grams);
+    d.sample = sampled ? 4u : 1u;
+    d.sfilter_bytes = (uint32_t)(simg.size() * 4);
+    d.sfilter_mode = smode;
+    d.sfilter_mask = smask_addr;
+    d.smap_bits = smap_bits;
+    d.s2_bytes = (uint32_t)(o_sfilter - o_grams);
     tb.n_grams = D;
     tb.filter_log2_bits = mode == kFilterNone ? 0 : fbits;
+    tb.sfilter_log2_bits = sampled ? sbits : 0;
     tb.bytes = std::move(b.bytes);
     return RK_OK;
 }
@@ -287,6 +354,8 @@ void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dm) {
     d->poff = (const uint64_t *)(dm + b.o_poff);
     d->plen = (const uint32_t *)(dm + b.o_plen);
     d->lengths = (const uint32_t *)(dm + b.o_lens);
+    d->smap = (const SampSlot *)(dm + b.o_smap);
+    d->sfilter = (const uint32_t *)(dm + b.o_sfilter);
     d->s2_base = dm + b.o_grams;
 }
 
@@ -314,10 +383,12 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
         return RK_EINVAL;
 
     TableBlob tb;
-    int rc = build_blob(patterns, lens, k, base_log2, o.filter, o.filter_log2_bits, &tb);
+    if (o.sample > 1) return RK_EINVAL;
+    int rc = build_blob(patterns, lens, k, base_log2, o.filter, o.filter_log2_bits, o.sample, &tb);
     if (rc) return rc;
     const uint32_t lmax = tb.meta.lmax;
-    const uint32_t fbytes = tb.meta.filter_bytes;
+    // either bit set (prefixes, or the sampled grams) is staged at offset 0
+    const uint32_t fbytes = std::max(tb.meta.filter_bytes, tb.meta.sfilter_bytes);
     const uint64_t s2_total = tb.meta.s2_bytes;
 
     int dev = 0, sms = 0, smem_optin = 0;
@@ -372,6 +443,7 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     t->tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
     t->n_grams = tb.n_grams;
     t->filter_log2_bits = tb.filter_log2_bits;
+    t->sfilter_log2_bits = tb.sfilter_log2_bits;
     t->filter_opt = o.filter;
     *out = t;
     return RK_OK;
@@ -421,6 +493,8 @@ extern "C" int rk_table_info_get(const rk_table *t, rk_table_info *info) {
     r.device = (uint32_t)t->device;
     r.s2_smem_bytes = t->tune.s2_smem;
     r.device_bytes = t->d_bytes;
+    r.sample_step = t->dev.sample;
+    r.sample_filter_log2_bits = t->sfilter_log2_bits;
     *info = r;
     return RK_OK;
 }

@@ -69,3 +69,35 @@ def assert_same(got, expect, what=""):
     assert gi.size == ei.size, f"{what}: {gi.size} matches, oracle {ei.size}"
     assert np.array_equal(gi.astype(np.uint64), ei.astype(np.uint64)), what
     assert np.array_equal(go.astype(np.uint64), eo.astype(np.uint64)), what
+
+
+def deferred_search(patterns: Sequence[bytes], text: np.ndarray, misalign: int = 0,
+                    via_search: bool = True, **opts) -> Tuple[np.ndarray, np.ndarray]:
+    """Sorted (ids, offsets) through the deferred scan (rk_search_device given
+    room for the candidate list, or rk_scan_device_ws + rk_sort_device);
+    grows the output until it fits."""
+    table = rk.rk_build(list(patterns), **opts)
+    try:
+        n = int(text.size)
+        d = to_device(text, misalign)
+        cap = max(1024, n // 8)
+        while True:
+            keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+            info = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+            sort_b = rk.rk_workspace_bytes(table, cap)
+            scan_b = rk.rk_scan_workspace_bytes(table, n)
+            ws = torch.empty(sort_b + scan_b, dtype=torch.uint8, device="cuda")
+            if via_search:
+                rk.rk_search_device(table, d if n else 0, n, keys, cap, info, ws, sort_b + scan_b)
+            else:
+                sws = torch.empty(scan_b, dtype=torch.uint8, device="cuda")
+                rk.rk_scan_device_ws(table, d if n else 0, n, keys, cap, info, sws, scan_b)
+                rk.rk_sort_device(table, n, keys, cap, info, ws, sort_b)
+            torch.cuda.synchronize()
+            count, status = (int(v) for v in info.cpu().tolist())
+            assert status == rk.RK_OK, rk.strerror(status)
+            if count <= cap:
+                return keys_to_pairs(keys[:count])
+            cap = count
+    finally:
+        rk.rk_destroy(table)

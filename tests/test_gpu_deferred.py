@@ -10,7 +10,7 @@ from workloads import make_config, random_small
 
 pytestmark = pytest.mark.gpu
 
-from gpu_util import assert_same, keys_to_pairs, require_gpu, to_device  # noqa: E402
+from gpu_util import assert_same, deferred_search, require_gpu  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -19,39 +19,6 @@ def _gpu():
 
 
 from paper_1810_01051_gb300 import rk  # noqa: E402
-
-torch = pytest.importorskip("torch")
-
-
-def deferred_search(patterns, text, misalign=0, via_search=True, **opts):
-    """Sorted (ids, offsets) through the deferred path; grows the output
-    until it fits."""
-    table = rk.rk_build(list(patterns), **opts)
-    try:
-        n = int(text.size)
-        d = to_device(text, misalign)
-        cap = max(1024, n // 8)
-        while True:
-            keys = torch.empty(cap, dtype=torch.int64, device="cuda")
-            info = torch.full((2,), -1, dtype=torch.int64, device="cuda")
-            sort_b = rk.rk_workspace_bytes(table, cap)
-            scan_b = rk.rk_scan_workspace_bytes(table, n)
-            ws = torch.empty(sort_b + scan_b, dtype=torch.uint8, device="cuda")
-            if via_search:
-                rk.rk_search_device(table, d if n else 0, n, keys, cap, info, ws, sort_b + scan_b)
-            else:
-                sws = torch.empty(scan_b, dtype=torch.uint8, device="cuda")
-                rk.rk_scan_device_ws(table, d if n else 0, n, keys, cap, info, sws, scan_b)
-                rk.rk_sort_device(table, n, keys, cap, info, ws, sort_b)
-            torch.cuda.synchronize()
-            count, status = (int(v) for v in info.cpu().tolist())
-            assert status == rk.RK_OK, rk.strerror(status)
-            if count <= cap:
-                return keys_to_pairs(keys[:count])
-            cap = count
-    finally:
-        rk.rk_destroy(table)
-
 
 OPTS = [
     dict(),
