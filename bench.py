@@ -159,6 +159,26 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+# ---------------------------------------------------------------- replicas
+
+def max_over_ranks(values, device="cpu"):
+    """Each value's maximum over all ranks (every rank passes its own
+    measurements); unchanged in a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_gbps(world, bytes_per_rank, steps, total_ms):
+    """Whole-job GB/s of `world` replicas: every rank's bytes over the
+    slowest rank's time."""
+    return world * bytes_per_rank * steps / (total_ms / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -601,10 +621,7 @@ def run_ours(args, rank, world, local_rank):
             except Exception as exc:  # a failed extra must not lose the main line
                 extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
 
     rk.rk_destroy(table)
     if rank != 0:
@@ -613,7 +630,7 @@ def run_ours(args, rank, world, local_rank):
         return 0
 
     step_ms = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3) / 1e9
+    value = job_gbps(world, n, args.steps, total_ms)
     scan_mean_s = statistics.mean(scan_ms) / 1e3
     alg_bytes = n + 8 * m
     peak, peak_src = hbm_peak()
@@ -651,7 +668,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": f"{peak_src} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": None if args.no_e2e else {
-            "value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n,
+            "value": job_gbps(world, n, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
             "d2h_bytes_per_step": 16 + 8 * m},
         "gpu_launches": args.steps * (scan_kernels + sort_kernels),
         "clocks": clocks,
