@@ -223,18 +223,31 @@ __global__ void __launch_bounds__(kThreads) rk_sort_pass_kernel(
     }
 }
 
+// Arrival with release semantics (gpu scope): the CTA's writes ordered
+// before it by the preceding __syncthreads are visible to any thread that
+// acquires the counter value.
+__device__ __forceinline__ void arrive_release(unsigned int *ctr) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+}
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *ctr) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    return v;
+}
+
 // Grid-wide barrier of a cooperative launch (every CTA resident): one
-// arrival counter in global memory, target = barriers passed x CTAs.  The
-// wait is bounded; on a timeout RK_ETIMEOUT is recorded and false returned.
+// arrival counter in global memory, target = barriers passed x CTAs; a
+// release arrival and acquire loads order the phases' memory.  The wait is
+// bounded; on a timeout RK_ETIMEOUT is recorded and false returned.
 __device__ __forceinline__ bool grid_sync(unsigned int *ctr, unsigned int target,
                                           unsigned long long *info, int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
+        arrive_release(ctr);
         int ok = 1;
         uint64_t t0 = 0;
-        while (*reinterpret_cast<volatile unsigned int *>(ctr) < target) {
+        while (load_acquire(ctr) < target) {
             const uint64_t now = globaltimer_ns();
             if (t0 == 0) {
                 t0 = now;
@@ -244,7 +257,6 @@ __device__ __forceinline__ bool grid_sync(unsigned int *ctr, unsigned int target
                 break;
             }
         }
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
