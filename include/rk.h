@@ -120,6 +120,18 @@ const char *rk_strerror(int status);
 int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t n_patterns,
              const rk_build_opts *opts, rk_table **out);
 
+/* The shape and launch configuration rk_build would give these patterns and
+ * options on a device whose opt-in shared memory per block is smem_optin
+ * bytes (cudaDevAttrMaxSharedMemoryPerBlockOptin; 232448 on GB300), worked
+ * out on the host: no CUDA call and no device memory, so a caller can size a
+ * table before building it.  Arguments as rk_build; info receives what
+ * rk_table_info_get would report for the built table, except sm_count (0)
+ * and device (UINT32_MAX); device_bytes is the size of the table's device
+ * allocation.  Errors: RK_EINVAL (as rk_build; null info; smem_optin too
+ * small for the requested CTAs per SM or for the longest pattern's halo).  */
+int rk_plan(const uint8_t *patterns, const uint32_t *lens, uint32_t n_patterns,
+            const rk_build_opts *opts, uint32_t smem_optin, rk_table_info *info);
+
 /* Free a table (NULL is ignored).  No search may be in flight on it. */
 void rk_destroy(rk_table *t);
 
@@ -159,7 +171,7 @@ int rk_sort_device(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t cap
 int rk_sort_launches(const rk_table *t, uint64_t n, uint64_t capacity, uint32_t *launches);
 
 /* Bytes of device workspace rk_scan_device_ws needs for a text of n bytes:
- * a candidate count and a list of up to n / 64 + 4096 candidates, 8 bytes
+ * a candidate count and a list of up to n / 64 + 4096 candidates, 16 bytes
  * each (0 on bad arguments). */
 uint64_t rk_scan_workspace_bytes(const rk_table *t, uint64_t n);
 

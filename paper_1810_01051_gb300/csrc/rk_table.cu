@@ -361,47 +361,65 @@ void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dm) {
 
 }  // namespace rk
 
-extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
-                        const rk_build_opts *opts, rk_table **out) {
-    if (!out) return RK_EINVAL;
-    *out = nullptr;
+namespace rk {
+namespace {
+
+// rk_build_opts with the defaults filled in.
+struct Opts {
+    uint32_t base_log2, filter, filter_log2_bits, warps, tile, stages, cps, sample;
+};
+
+// Check the patterns' count and lengths and the options (no CUDA call).
+int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
+              const rk_build_opts *opts, Opts *out) {
     if (k > RK_MAX_PATTERNS) return RK_EINVAL;
     if (k > 0 && (!patterns || !lens)) return RK_EINVAL;
+    for (uint32_t i = 0; i < k; ++i)
+        if (lens[i] < 1 || lens[i] > RK_MAX_PATTERN_LEN) return RK_EINVAL;
     rk_build_opts o{};
     if (opts) o = *opts;
-    uint32_t base_log2 = o.base_log2 ? o.base_log2 : 8;
-    if (base_log2 < 1 || base_log2 > 60) return RK_EINVAL;
-    if (o.filter > RK_FILTER_NONE) return RK_EINVAL;
-    uint32_t warps = o.warps ? o.warps : 24;
+    Opts r{};
+    r.base_log2 = o.base_log2 ? o.base_log2 : 8;
+    r.filter = o.filter;
+    r.filter_log2_bits = o.filter_log2_bits;
+    r.warps = o.warps ? o.warps : 24;
     // default: 48 KiB tiles (two 24 KiB rounds of 24 warps), two in flight
-    uint32_t tile = o.tile_bytes ? o.tile_bytes : 49152;
-    uint32_t stages = o.stages ? o.stages : 2;
-    uint32_t cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
+    r.tile = o.tile_bytes ? o.tile_bytes : 49152;
+    r.stages = o.stages ? o.stages : 2;
+    r.cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
+    r.sample = o.sample;
+    if (r.base_log2 < 1 || r.base_log2 > 60) return RK_EINVAL;
+    if (r.filter > RK_FILTER_NONE) return RK_EINVAL;
     // survivor positions within a tile are 16-bit
-    if (warps < 1 || warps > 31 || tile < 1024 || tile % 16 || tile > kMaxTileBytes ||
-        stages < 2 || stages > 8 || cps < 1 || cps > 8)
+    if (r.warps < 1 || r.warps > 31 || r.tile < 1024 || r.tile % 16 || r.tile > kMaxTileBytes ||
+        r.stages < 2 || r.stages > 8 || r.cps < 1 || r.cps > 8)
         return RK_EINVAL;
+    if (r.sample > 1) return RK_EINVAL;
+    *out = r;
+    return RK_OK;
+}
 
-    TableBlob tb;
-    if (o.sample > 1) return RK_EINVAL;
-    int rc = build_blob(patterns, lens, k, base_log2, o.filter, o.filter_log2_bits, o.sample, &tb);
+// Host part of rk_build: build the host image of the table and pick the
+// launch shape for a device with smem_optin bytes of opt-in shared memory per
+// block.  No CUDA call.
+int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const Opts &o,
+               uint32_t smem_optin, TableBlob *tb, Tuning *tune) {
+    uint32_t tile = o.tile, stages = o.stages;
+    const uint32_t warps = o.warps, cps = o.cps;
+    // room for the static shared memory of each CTA
+    if (smem_optin / cps <= 1024) return RK_EINVAL;
+
+    int rc = build_blob(patterns, lens, k, o.base_log2, o.filter, o.filter_log2_bits, o.sample,
+                        tb);
     if (rc) return rc;
-    const uint32_t lmax = tb.meta.lmax;
+    const uint32_t lmax = tb->meta.lmax;
     // either bit set (prefixes, or the sampled grams) is staged at offset 0
-    const uint32_t fbytes = std::max(tb.meta.filter_bytes, tb.meta.sfilter_bytes);
-    const uint64_t s2_total = tb.meta.s2_bytes;
-
-    int dev = 0, sms = 0, smem_optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return RK_ECUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return RK_ECUDA;
-    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
-        cudaSuccess)
-        return RK_ECUDA;
+    const uint32_t fbytes = std::max(tb->meta.filter_bytes, tb->meta.sfilter_bytes);
+    const uint64_t s2_total = tb->meta.s2_bytes;
 
     // ---- launch shape: shrink stages / tile until shared memory fits -------
     uint32_t halo = align_up(std::max<uint32_t>(lmax - 1, 1), 16);
-    uint32_t limit = (uint32_t)smem_optin / cps - 1024;  // room for static shared memory
+    uint32_t limit = smem_optin / cps - 1024;
     // The survivor-stage tables go to shared memory when they fit beside the
     // requested pipeline (or beside a two-stage one); otherwise they are read
     // from global memory (L2).
@@ -422,6 +440,65 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
         tile = tile / 16 * 16;
         lay = smem_layout(fbytes, s2, warps, stages, tile, halo);
     }
+    *tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
+    return RK_OK;
+}
+
+rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
+                        uint32_t filter_log2_bits, uint32_t sfilter_log2_bits, uint32_t sm_count,
+                        uint32_t device, uint64_t device_bytes) {
+    rk_table_info r{};
+    r.n_patterns = d.n_patterns;
+    r.min_len = d.lmin;
+    r.max_len = d.lmax;
+    r.n_lengths = d.n_lengths;
+    r.gram_len = d.q;
+    r.base_log2 = d.base_log2;
+    r.filter = d.filter_mode == kFilterNone ? RK_FILTER_NONE
+               : d.filter_mode == kFilterReplicated ? RK_FILTER_REPLICATED
+                                                    : RK_FILTER_FLAT;
+    r.filter_log2_bits = filter_log2_bits;
+    r.filter_smem_bytes = d.filter_bytes;
+    r.n_grams = n_grams;
+    r.warps = tune.warps;
+    r.tile_bytes = tune.tile_bytes;
+    r.stages = tune.stages;
+    r.ctas_per_sm = tune.ctas_per_sm;
+    r.halo_bytes = tune.halo;
+    r.smem_bytes = tune.smem_bytes;
+    r.sm_count = sm_count;
+    r.device = device;
+    r.s2_smem_bytes = tune.s2_smem;
+    r.device_bytes = device_bytes;
+    r.sample_step = d.sample;
+    r.sample_filter_log2_bits = sfilter_log2_bits;
+    return r;
+}
+
+}  // namespace
+}  // namespace rk
+
+extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
+                        const rk_build_opts *opts, rk_table **out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    // bad patterns and options are rejected before any CUDA call
+    Opts o{};
+    int rc = read_opts(patterns, lens, k, opts, &o);
+    if (rc) return rc;
+
+    int dev = 0, sms = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RK_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RK_ECUDA;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+        return RK_ECUDA;
+
+    TableBlob tb;
+    Tuning tune{};
+    rc = plan_table(patterns, lens, k, o, (uint32_t)smem_optin, &tb, &tune);
+    if (rc) return rc;
 
     rk_table *t = new (std::nothrow) rk_table();
     if (!t) return RK_ENOMEM;
@@ -440,12 +517,27 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
         return RK_ECUDA;
     }
     bind_blob(&t->dev, tb, (const uint8_t *)t->d_mem);
-    t->tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
+    t->tune = tune;
     t->n_grams = tb.n_grams;
     t->filter_log2_bits = tb.filter_log2_bits;
     t->sfilter_log2_bits = tb.sfilter_log2_bits;
     t->filter_opt = o.filter;
     *out = t;
+    return RK_OK;
+}
+
+extern "C" int rk_plan(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
+                       const rk_build_opts *opts, uint32_t smem_optin, rk_table_info *info) {
+    if (!info) return RK_EINVAL;
+    Opts o{};
+    int rc = read_opts(patterns, lens, k, opts, &o);
+    if (rc) return rc;
+    TableBlob tb;
+    Tuning tune{};
+    rc = plan_table(patterns, lens, k, o, smem_optin, &tb, &tune);
+    if (rc) return rc;
+    *info = make_info(tb.meta, tune, tb.n_grams, tb.filter_log2_bits, tb.sfilter_log2_bits, 0,
+                      UINT32_MAX, tb.bytes.size());
     return RK_OK;
 }
 
@@ -470,31 +562,7 @@ extern "C" void rk_destroy(rk_table *t) {
 
 extern "C" int rk_table_info_get(const rk_table *t, rk_table_info *info) {
     if (!t || !info) return RK_EINVAL;
-    rk_table_info r{};
-    r.n_patterns = t->dev.n_patterns;
-    r.min_len = t->dev.lmin;
-    r.max_len = t->dev.lmax;
-    r.n_lengths = t->dev.n_lengths;
-    r.gram_len = t->dev.q;
-    r.base_log2 = t->dev.base_log2;
-    r.filter = t->dev.filter_mode == kFilterNone ? RK_FILTER_NONE
-               : t->dev.filter_mode == kFilterReplicated ? RK_FILTER_REPLICATED
-                                                          : RK_FILTER_FLAT;
-    r.filter_log2_bits = t->filter_log2_bits;
-    r.filter_smem_bytes = t->dev.filter_bytes;
-    r.n_grams = t->n_grams;
-    r.warps = t->tune.warps;
-    r.tile_bytes = t->tune.tile_bytes;
-    r.stages = t->tune.stages;
-    r.ctas_per_sm = t->tune.ctas_per_sm;
-    r.halo_bytes = t->tune.halo;
-    r.smem_bytes = t->tune.smem_bytes;
-    r.sm_count = (uint32_t)t->sm_count;
-    r.device = (uint32_t)t->device;
-    r.s2_smem_bytes = t->tune.s2_smem;
-    r.device_bytes = t->d_bytes;
-    r.sample_step = t->dev.sample;
-    r.sample_filter_log2_bits = t->sfilter_log2_bits;
-    *info = r;
+    *info = make_info(t->dev, t->tune, t->n_grams, t->filter_log2_bits, t->sfilter_log2_bits,
+                      (uint32_t)t->sm_count, (uint32_t)t->device, t->d_bytes);
     return RK_OK;
 }

@@ -27,7 +27,7 @@ RK_NOALLOC_MAX_KEYS = 1 << 20
 
 #: names of every function include/rk.h declares
 EXPORTS = [
-    "rk_strerror", "rk_build", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
+    "rk_strerror", "rk_build", "rk_plan", "rk_destroy", "rk_table_info_get", "rk_workspace_bytes",
     "rk_sort_launches", "rk_scan_workspace_bytes", "rk_scan_device_ws", "rk_scan_launches",
     "rk_scan_device", "rk_sort_device", "rk_search_device", "rk_search",
     "rk_window_hashes_device", "rk_search_device_noalloc",
@@ -111,6 +111,8 @@ def load() -> ctypes.CDLL:
     L.rk_strerror.argtypes = [ctypes.c_int]
     L.rk_build.restype = ctypes.c_int
     L.rk_build.argtypes = [vp, vp, u32, ctypes.POINTER(BuildOpts), ctypes.POINTER(vp)]
+    L.rk_plan.restype = ctypes.c_int
+    L.rk_plan.argtypes = [vp, vp, u32, ctypes.POINTER(BuildOpts), u32, ctypes.POINTER(TableInfo)]
     L.rk_destroy.restype = None
     L.rk_destroy.argtypes = [vp]
     L.rk_table_info_get.restype = ctypes.c_int
@@ -222,6 +224,28 @@ def rk_build(patterns: Sequence[bytes], base_log2: int = 0, filter: int = RK_FIL
                       lens.ctypes.data if len(patterns) else None,
                       len(patterns), ctypes.byref(opts), ctypes.byref(out)), "rk_build")
     return int(out.value)
+
+
+#: opt-in shared memory per block of a GB300 (cudaDevAttrMaxSharedMemoryPerBlockOptin)
+GB300_SMEM_OPTIN = 232448
+
+
+def rk_plan(patterns: Sequence[bytes], smem_optin: int = GB300_SMEM_OPTIN, base_log2: int = 0,
+            filter: int = RK_FILTER_AUTO, filter_log2_bits: int = 0, warps: int = 0,
+            tile_bytes: int = 0, stages: int = 0, ctas_per_sm: int = 0, sample: int = 0) -> dict:
+    """What rk_build would give these patterns on a device with `smem_optin`
+    bytes of opt-in shared memory per block, worked out on the host (no GPU);
+    the keys of rk_table_info."""
+    L = load()
+    lens = np.array([len(p) for p in patterns], dtype=np.uint32)
+    cat = np.frombuffer(b"".join(bytes(p) for p in patterns) or b"\0", dtype=np.uint8).copy()
+    opts = BuildOpts(base_log2, filter, filter_log2_bits, warps, tile_bytes, stages, ctas_per_sm,
+                     sample)
+    info = TableInfo()
+    _check(L.rk_plan(cat.ctypes.data if len(patterns) else None,
+                     lens.ctypes.data if len(patterns) else None,
+                     len(patterns), ctypes.byref(opts), smem_optin, ctypes.byref(info)), "rk_plan")
+    return {name: getattr(info, name) for name, _ in TableInfo._fields_}
 
 
 def rk_destroy(table: int) -> None:
