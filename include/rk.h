@@ -184,8 +184,10 @@ uint64_t rk_scan_workspace_bytes(const rk_table *t, uint64_t n);
  * the unsorted keys differs).  Windows offered beyond the list's room are
  * verified inside the scan as rk_scan_device does.
  *   d_workspace  at least rk_scan_workspace_bytes(t, n) bytes, 16-byte
- *                aligned, not shared with a call in flight; a smaller (or
- *                null) workspace, or a table built with RK_FILTER_NONE,
+ *                aligned, not shared with a call in flight; a smaller,
+ *                unaligned or null workspace, a table built with
+ *                RK_FILTER_NONE, or one with more than 2^23 distinct q-byte
+ *                prefixes (a candidate holds its prefix-map slot in 24 bits)
  *                runs rk_scan_device instead.
  * Other arguments, results and errors as rk_scan_device.                    */
 int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
@@ -200,10 +202,13 @@ int rk_scan_launches(const rk_table *t, uint64_t n, uint64_t workspace_bytes,
                      uint32_t *launches);
 
 /* rk_scan_device followed by rk_sort_device on one stream: the sorted match
- * list of d_text[0..n) in d_keys, its length in d_info[0].  A workspace of
- * rk_workspace_bytes(t, capacity) + rk_scan_workspace_bytes(t, n) bytes
- * makes the scan part run as rk_scan_device_ws (its list placed after the
- * sort's workspace).                                                         */
+ * list of d_text[0..n) in d_keys, its length in d_info[0].
+ *   d_workspace  16-byte aligned; at least rk_workspace_bytes(t, capacity)
+ *                bytes when capacity >= 2 (the sort's).  With
+ *                rk_workspace_bytes(t, capacity) + rk_scan_workspace_bytes(t, n)
+ *                bytes the scan part runs as rk_scan_device_ws, its list
+ *                placed after the sort's workspace.
+ * Errors: as rk_scan_device and rk_sort_device.                              */
 int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
                      uint64_t capacity, uint64_t *d_info, void *d_workspace,
                      uint64_t workspace_bytes, void *stream);
