@@ -135,6 +135,8 @@ int rk_plan(const uint8_t *patterns, const uint32_t *lens, uint32_t n_patterns,
 /* Free a table (NULL is ignored).  No search may be in flight on it. */
 void rk_destroy(rk_table *t);
 
+/* Read back a table's shape and launch configuration (host only, no CUDA
+ * call).  Errors: RK_EINVAL (t or info NULL).                               */
 int rk_table_info_get(const rk_table *t, rk_table_info *info);
 
 /* Bytes of device workspace rk_sort_device / rk_search_device need for an
@@ -271,6 +273,7 @@ typedef struct rk_batch rk_batch;
 int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, const uint32_t *lens,
                       const uint32_t *patterns_per_table, const rk_build_opts *opts,
                       rk_tableset **out);
+/* Free a table set (NULL is ignored).  No batch or server may still use it. */
 void rk_tableset_destroy(rk_tableset *ts);
 
 typedef struct rk_batch_opts {
@@ -296,7 +299,12 @@ typedef struct rk_batch_info {
  * captured graph.  The table set must outlive the batch.
  * Errors: RK_EINVAL (limits, fields wider than 64 bits), RK_ENOMEM, RK_ECUDA. */
 int rk_batch_create(const rk_tableset *ts, const rk_batch_opts *opts, rk_batch **out);
+/* Free a batch engine (NULL is ignored) after its capture stream drains; a
+ * run on a caller stream must have completed.                               */
 void rk_batch_destroy(rk_batch *b);
+/* Key field widths, the launch shape in use (after rk_batch_autotune, the
+ * one it kept) and the work chunks of the current batch (host only).
+ * Errors: RK_EINVAL (b or info NULL).                                       */
 int rk_batch_info_get(const rk_batch *b, rk_batch_info *info);
 
 /* Describe the next batch: item i searches d_texts[i][0 .. text_lens[i]) (device
@@ -313,7 +321,8 @@ int rk_batch_run(rk_batch *b, void *stream);
 /* Device pointers owned by the batch (valid until rk_batch_destroy): the
  * sorted keys, n_items + 1 item offsets into them (item i's matches are keys
  * [offsets[i], offsets[i+1])), and the header {count, status}.  When count >
- * capacity the keys and offsets are not valid.                              */
+ * capacity the keys and offsets are not valid.  Any output pointer may be
+ * NULL.  Errors: RK_EINVAL (b NULL).                                        */
 int rk_batch_results(const rk_batch *b, const uint64_t **d_keys, const uint64_t **d_item_offsets,
                      const uint64_t **d_info);
 
@@ -324,10 +333,14 @@ int rk_batch_results(const rk_batch *b, const uint64_t **d_keys, const uint64_t 
 int rk_batch_read(const rk_batch *b, uint64_t *h_keys, uint64_t key_cap, uint64_t *h_item_offsets,
                   uint64_t *h_info, void *stream);
 
-/* Autotuner: time up to max_candidates launch shapes (tile size, warps,
- * stages, CTAs per SM, survivor-table placement; 0 = all that fit), each
- * `reps` times on the current batch, keep the fastest and re-capture the
- * graph.  *best_ms (may be NULL) gets the best scan time.  Synchronous.     */
+/* Autotuner (the paper's threads-per-block sweep of Table 1, automated):
+ * time up to max_candidates launch shapes (tile size, warps, stages, CTAs
+ * per SM, survivor-table placement; 0 = all that fit, else an even spread of
+ * them), each `reps` times (0: 3) on the current batch, keep the fastest and
+ * re-capture the graph.  *best_ms (may be NULL) gets the best time of one
+ * run, or -1 when no shape could run (the previous shape is kept).
+ * Synchronous; the batch's results are overwritten.
+ * Errors: RK_EINVAL (b NULL), RK_ENOMEM, RK_ECUDA.                          */
 int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t reps, double *best_ms,
                       void *stream);
 
@@ -381,6 +394,11 @@ int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_text, uint64
 int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms, uint64_t *h_keys,
                    uint64_t key_cap, uint64_t *n_keys, rk_request_times *times);
 
+/* Counters of the server (a consistent snapshot): requests and bytes done,
+ * batches launched and requests they held, requests waiting for admission,
+ * requests admitted and not finished (in_flight: copying, queued for an
+ * engine or running), arena bytes in use, and the server's clock.
+ * Errors: RK_EINVAL (s or stats NULL).                                      */
 int rk_server_stats_get(rk_server *s, rk_server_stats *stats);
 
 /* ---- search without allocation ------------------------------------------
