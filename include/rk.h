@@ -389,8 +389,9 @@ int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_text, uint64
 /* Wait up to timeout_ms (< 0: forever) for a request and take its result:
  * *n_keys gets the match count, h_keys[0..n_keys) the sorted keys, *times
  * (may be NULL) its timestamps.  RK_ECAPACITY: key_cap < *n_keys, the result
- * is kept (call again); RK_ETIMEOUT: not finished yet.  Other errors: the
- * request failed and is released.                                           */
+ * is kept (call again); RK_ETIMEOUT: not finished yet; RK_EINVAL: no such
+ * request (never submitted, or already taken).  Other errors (RK_ECUDA: its
+ * copy or batch failed): the request failed and is released.                */
 int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms, uint64_t *h_keys,
                    uint64_t key_cap, uint64_t *n_keys, rk_request_times *times);
 

@@ -15,6 +15,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "rk_internal.cuh"
 
@@ -112,10 +113,10 @@ struct rk_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> arrived, copying, ready;
     std::unordered_map<uint64_t, Request *> finished;
+    std::unordered_set<uint64_t> open_ids;  // submitted and not yet taken
     uint64_t next_id = 1;
     uint32_t batch_limit = 0;  // items per batch after an overflow (0: no limit)
     bool stop = false;
-    int fatal = RK_OK;
     uint64_t bytes_done = 0, requests_done = 0, batches = 0, items_batched = 0;
     std::vector<cudaEvent_t> spare_events;
     std::thread worker;
@@ -212,24 +213,48 @@ void loop(rk_server *s) {
             r->on_arena = true;
             r->t_admit = s->now_us();
             r->copied = take_event(s);
-            if (r->n)
-                cudaMemcpyAsync(s->arena_mem + off, r->h_text, r->n, cudaMemcpyHostToDevice,
-                                s->copy_stream);
-            cudaEventRecord(r->copied, s->copy_stream);
-            s->copying.push_back(r);
             progress = true;
+            bool ok = r->copied != nullptr;
+            if (ok && r->n)
+                ok = cudaMemcpyAsync(s->arena_mem + off, r->h_text, r->n, cudaMemcpyHostToDevice,
+                                     s->copy_stream) == cudaSuccess;
+            if (ok) ok = cudaEventRecord(r->copied, s->copy_stream) == cudaSuccess;
+            if (!ok) {
+                // no copy may still write into the arena block being released
+                cudaStreamSynchronize(s->copy_stream);
+                cudaGetLastError();
+                finish(s, r, RK_ECUDA);
+                continue;
+            }
+            s->copying.push_back(r);
         }
         // 2. texts that have landed become ready, in arrival order
-        while (!s->copying.empty() && cudaEventQuery(s->copying.front()->copied) == cudaSuccess) {
-            s->ready.push_back(s->copying.front());
+        while (!s->copying.empty()) {
+            const cudaError_t q = cudaEventQuery(s->copying.front()->copied);
+            if (q == cudaErrorNotReady) break;
+            Request *r = s->copying.front();
             s->copying.pop_front();
             progress = true;
+            if (q == cudaSuccess) {
+                s->ready.push_back(r);
+            } else {
+                cudaGetLastError();
+                finish(s, r, RK_ECUDA);
+            }
         }
         // 3. finished batches hand back results and memory
         for (Engine &e : s->engines) {
-            if (e.busy && cudaEventQuery(e.done) == cudaSuccess) {
+            if (!e.busy) continue;
+            const cudaError_t q = cudaEventQuery(e.done);
+            if (q == cudaErrorNotReady) continue;
+            progress = true;
+            if (q == cudaSuccess) {
                 harvest(s, e);
-                progress = true;
+            } else {
+                cudaGetLastError();
+                for (Request *r : e.reqs) finish(s, r, RK_ECUDA);
+                e.reqs.clear();
+                e.busy = false;
             }
         }
         if (progress) s->cv_done.notify_all();
@@ -388,6 +413,7 @@ extern "C" int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_t
         r->id = s->next_id++;
         r->t_arrive = s->now_us();
         s->arrived.push_back(r);
+        s->open_ids.insert(r->id);
         *request_id = r->id;
     }
     s->cv_work.notify_one();
@@ -398,6 +424,7 @@ extern "C" int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms,
                               uint64_t key_cap, uint64_t *n_keys, rk_request_times *times) {
     if (!s || !n_keys) return RK_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
+    if (!s->open_ids.count(request_id)) return RK_EINVAL;  // never submitted, or taken
     auto pred = [&] { return s->finished.count(request_id) != 0; };
     if (timeout_ms < 0) s->cv_done.wait(lk, pred);
     else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
@@ -413,12 +440,14 @@ extern "C" int rk_server_take(rk_server *s, uint64_t request_id, int timeout_ms,
     if (r->status != RK_OK) {
         const int st = r->status;
         s->finished.erase(request_id);
+        s->open_ids.erase(request_id);
         delete r;
         return st;
     }
     if (r->keys.size() > key_cap) return RK_ECAPACITY;  // kept: call again with a larger buffer
     if (h_keys && !r->keys.empty()) std::copy(r->keys.begin(), r->keys.end(), h_keys);
     s->finished.erase(request_id);
+    s->open_ids.erase(request_id);
     delete r;
     return RK_OK;
 }

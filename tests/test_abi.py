@@ -97,3 +97,33 @@ def test_unpack_keys():
     keys = np.array([(5 << 40) | 17, (0 << 40) | ((1 << 40) - 1)], dtype=np.uint64)
     ids, offs = rk.unpack_keys(keys)
     assert ids.tolist() == [5, 0] and offs.tolist() == [17, (1 << 40) - 1]
+
+
+def test_handle_entry_points_reject_null(lib):
+    # every call on a batch, table set or server checks its handle before any
+    # CUDA call; the destroys ignore NULL
+    n = ctypes.c_uint64(5)
+    out = ctypes.c_void_p(9)
+    assert lib.rk_tableset_build(0, None, None, None, None, ctypes.byref(out)) == rk.RK_EINVAL
+    assert lib.rk_batch_create(None, None, ctypes.byref(out)) == rk.RK_EINVAL
+    assert out.value is None  # cleared on error
+    assert lib.rk_batch_set(None, 0, None, None, None, None) == rk.RK_EINVAL
+    assert lib.rk_batch_run(None, None) == rk.RK_EINVAL
+    assert lib.rk_batch_results(None, None, None, None) == rk.RK_EINVAL
+    info = (ctypes.c_uint64 * 2)()
+    assert lib.rk_batch_read(None, None, 0, None, info, None) == rk.RK_EINVAL
+    assert lib.rk_batch_autotune(None, 0, 0, None, None) == rk.RK_EINVAL
+    assert lib.rk_batch_info_get(None, None) == rk.RK_EINVAL
+    assert lib.rk_server_create(None, None, ctypes.byref(out)) == rk.RK_EINVAL
+    assert lib.rk_server_submit(None, 0, None, 0, ctypes.byref(n)) == rk.RK_EINVAL
+    assert lib.rk_server_take(None, 1, 0, None, 0, ctypes.byref(n), None) == rk.RK_EINVAL
+    assert lib.rk_server_stats_get(None, None) == rk.RK_EINVAL
+    assert lib.rk_search_device_noalloc(None, None, 0, None, 0, None, None) == rk.RK_EINVAL
+    # the paper's kernel checks its pattern and launch shape first
+    pat = np.frombuffer(b"ACGT", dtype=np.uint8).copy()
+    assert lib.rk_paper_search_device(None, 10, None, 4, None, 0, None) == rk.RK_EINVAL
+    assert lib.rk_paper_search_device(None, 10, pat.ctypes.data, 0, None, 0, None) == rk.RK_EINVAL
+    assert lib.rk_paper_search_device(None, 10, pat.ctypes.data, 4, None, 48, None) == rk.RK_EINVAL
+    lib.rk_batch_destroy(None)
+    lib.rk_tableset_destroy(None)
+    lib.rk_server_destroy(None)

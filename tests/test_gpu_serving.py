@@ -90,5 +90,10 @@ def test_submit_rejects_bad_requests(tableset):
         rid = rk.rk_server_submit(s, 1, empty, 0)
         rc, keys, _ = rk.rk_server_take(s, rid, timeout_ms=10000)
         assert rc == rk.RK_OK and keys.size == 0
+        # a request already taken, or an id never issued, is refused at once
+        # (a bounded wait, so that a regression fails instead of hanging)
+        for bad in (rid, rid + 1000):
+            rc, _, _ = rk.rk_server_take(s, bad, timeout_ms=2000)
+            assert rc == rk.RK_EINVAL
     finally:
         rk.rk_server_destroy(s)
