@@ -310,7 +310,10 @@ int rk_batch_info_get(const rk_batch *b, rk_batch_info *info);
 /* Describe the next batch: item i searches d_texts[i][0 .. text_lens[i]) (device
  * memory, any alignment, kept valid until the run completes) with table
  * table_of_item[i].  Host arrays; the descriptors are copied on `stream` and
- * the call returns once they are on the device.  Errors: RK_EINVAL, RK_ECUDA. */
+ * the call returns once they are on the device, so a run of this batch on
+ * another stream must have completed.  Errors: RK_EINVAL (limits of
+ * rk_batch_opts exceeded, a table index out of range, another current
+ * device), RK_ECUDA.                                                        */
 int rk_batch_set(rk_batch *b, uint32_t n_items, const uint32_t *table_of_item,
                  const uint8_t *const *d_texts, const uint64_t *text_lens, void *stream);
 
@@ -337,8 +340,9 @@ int rk_batch_read(const rk_batch *b, uint64_t *h_keys, uint64_t key_cap, uint64_
  * time up to max_candidates launch shapes (tile size, warps, stages, CTAs
  * per SM, survivor-table placement; 0 = all that fit, else an even spread of
  * them), each `reps` times (0: 3) on the current batch, keep the fastest and
- * re-capture the graph.  *best_ms (may be NULL) gets the best time of one
- * run, or -1 when no shape could run (the previous shape is kept).
+ * re-capture the graph.  Only the scan is timed (the sort's work does not
+ * depend on the shape).  *best_ms (may be NULL) gets the best scan time, or
+ * -1 when no shape could run (the previous shape is kept).
  * Synchronous; the batch's results are overwritten.
  * Errors: RK_EINVAL (b NULL), RK_ENOMEM, RK_ECUDA.                          */
 int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t reps, double *best_ms,

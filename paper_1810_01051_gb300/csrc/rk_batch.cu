@@ -719,8 +719,11 @@ extern "C" int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t 
             pick.push_back(cand[(size_t)i * cand.size() / max_candidates]);
         cand.swap(pick);
     }
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RK_ECUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return RK_ECUDA;
+    }
     float best = -1.f;
     rk_batch_opts best_o = keep;
     for (const rk_batch_opts &o : cand) {
