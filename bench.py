@@ -101,18 +101,23 @@ def scan_sources_sha256():
     return h.hexdigest()
 
 
-def read_profile_traffic():
-    """DRAM bytes per scan launch from the committed ncu summary, if it was
-    taken on the current scan kernel sources (else None)."""
+def read_profile():
+    """Figures of the committed ncu summary of the scan step, if it was taken
+    on the current scan kernel sources (else None): DRAM bytes per step and
+    the tile scan's integer-pipe fractions."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
     m_src = re.search(r"scan_sources_sha256:\s*([0-9a-f]{64})", txt)
-    m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
-    if not (m_src and m_tr):
+    if not m_src or m_src.group(1) != scan_sources_sha256():
         return None
-    return float(m_tr.group(1)) if m_src.group(1) == scan_sources_sha256() else None
+    out = {}
+    for key in ("dram_bytes_per_full_launch", "tile_scan_alu_pipe_frac",
+                "tile_scan_fmaheavy_pipe_frac", "tile_scan_issue_active_frac"):
+        m = re.search(key + r":\s*([0-9.eE+]+)", txt)
+        out[key] = float(m.group(1)) if m else None
+    return out
 
 
 class ClockSampler:
@@ -635,7 +640,15 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = n + 8 * m
     peak, peak_src = hbm_peak()
     achieved = alg_bytes / scan_mean_s / 1e9
-    traffic = read_profile_traffic()
+    prof = read_profile() or {}
+    traffic = prof.get("dram_bytes_per_full_launch")
+    pipes = None
+    if prof.get("tile_scan_alu_pipe_frac") is not None:
+        pipes = {"kernel": "rk_scan_tiles_kernel",
+                 "alu_pipe_frac": prof["tile_scan_alu_pipe_frac"],
+                 "fmaheavy_pipe_frac": prof["tile_scan_fmaheavy_pipe_frac"],
+                 "issue_active_frac": prof["tile_scan_issue_active_frac"],
+                 "source": "ncu --set full of the same scan step (profiles/rk_scan_zipf_1GiB.md)"}
 
     cpu = None
     if pool is not None:
@@ -666,7 +679,8 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": ("rk_scan_tiles_kernel + rk_verify_kernel (timed together)"
                                 if scan_kernels == 2 else "rk_scan_tiles_kernel"),
                      "peak_source": f"{peak_src} hbm_gbs",
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "integer_pipes": pipes},
         "e2e": None if args.no_e2e else {
             "value": job_gbps(world, n, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
             "d2h_bytes_per_step": 16 + 8 * m},
