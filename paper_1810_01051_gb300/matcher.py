@@ -32,17 +32,20 @@ class Matcher:
 
     def search(self, text: torch.Tensor, capacity: Optional[int] = None,
                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
-        """Sorted match keys (id << 40 | x) of a uint8 CUDA tensor."""
+        """Sorted match keys (id << 40 | x) of a uint8 CUDA tensor.  The
+        workspace holds the sort's scratch and the candidate list, so the
+        scan verifies its survivors in a second kernel when the table allows."""
         assert text.is_cuda and text.dtype == torch.uint8 and text.is_contiguous()
         n = text.numel()
         cap = capacity if capacity is not None else max(1024, n // 256)
         st = stream or torch.cuda.current_stream(text.device)
+        scan_b = rk.rk_scan_workspace_bytes(self.table, n)
         while True:
             keys = torch.empty(max(cap, 1), dtype=torch.int64, device=text.device)
             info = torch.zeros(2, dtype=torch.int64, device=text.device)
-            wsb = rk.rk_workspace_bytes(self.table, cap)
+            wsb = rk.rk_workspace_bytes(self.table, cap) + scan_b
             ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=text.device)
-            rk.rk_search_device(self.table, text, n, keys, cap, info, ws, wsb, st)
+            rk.rk_search_device(self.table, text if n else 0, n, keys, cap, info, ws, wsb, st)
             st.synchronize()
             count, status = (int(v) for v in info.cpu().tolist())
             if status != rk.RK_OK:

@@ -198,3 +198,22 @@ def test_sort_paths_agree(n, k, lmin, lmax):
             assert_same(keys_to_pairs(keys[:count]), expect, f"cap {cap}")
     finally:
         rk.rk_destroy(table)
+
+
+def test_matcher_wrapper():
+    """The convenience wrapper (deferred scan through its workspace) gives the
+    oracle's list, grows a one-key output until it fits, and handles an
+    empty text."""
+    torch = pytest.importorskip("torch")
+    from paper_1810_01051_gb300.matcher import Matcher
+    w = make_config(1, n=3 << 20)
+    expect = oracle.rabin_karp(w.text, w.patterns)
+    m = Matcher(w.patterns)
+    try:
+        d = to_device(w.text)
+        for cap in (None, 1):
+            keys = m.search(d, capacity=cap)
+            assert_same(keys_to_pairs(keys), expect, f"capacity {cap}")
+        assert m.search(torch.zeros(0, dtype=torch.uint8, device="cuda")).numel() == 0
+    finally:
+        m.close()
