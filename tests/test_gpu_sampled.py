@@ -104,3 +104,18 @@ def test_short_pattern_disables_sampling():
     assert sample_step([b"abcdefg", b"abcdef"]) == 1
     assert sample_step([b"abcdefg", b"abcdefgh"]) == 4
     assert sample_step([b"abcdefg"], filter=rk.RK_FILTER_NONE) == 1
+
+
+def test_list_overflow_sampled():
+    """Sampled stage 1 with every window a candidate: each sampled position
+    offers the windows at all four of its gram's offsets, the list (n / 64 +
+    4096 entries) fills, and the rest are verified inside the scan."""
+    n = 1 << 20
+    text = np.full(n, ord("a"), dtype=np.uint8)
+    text[::1009] = ord("b")
+    pats = [b"aaaaaaa", b"aaaaaaaa", b"aaaaaaaaaaa", b"aaaaaaaaaaaab", b"baaaaaa"]
+    assert sample_step(pats) == 4
+    expect = oracle.bruteforce(text, pats)
+    assert expect[0].size > n // 64 + 4096
+    for mis in (0, 3):
+        assert_same(deferred_search(pats, text, mis), expect, f"overflow mis {mis}")
