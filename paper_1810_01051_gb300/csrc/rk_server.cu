@@ -17,62 +17,13 @@
 #include <unordered_map>
 #include <unordered_set>
 
+#include "rk_arena.h"
 #include "rk_internal.cuh"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
-
-// First-fit allocator over one device arena (offsets, 256-byte granules).
-class Arena {
-  public:
-    void reset(uint64_t bytes) {
-        free_.clear();
-        free_[0] = bytes;
-        used_ = 0;
-    }
-    bool alloc(uint64_t n, uint64_t *off) {
-        n = (n + 255) / 256 * 256;
-        if (n == 0) n = 256;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < n) continue;
-            *off = it->first;
-            const uint64_t rest = it->second - n, at = it->first + n;
-            free_.erase(it);
-            if (rest) free_[at] = rest;
-            used_ += n;
-            sizes_[*off] = n;
-            return true;
-        }
-        return false;
-    }
-    void release(uint64_t off) {
-        auto s = sizes_.find(off);
-        if (s == sizes_.end()) return;
-        uint64_t n = s->second;
-        sizes_.erase(s);
-        used_ -= n;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + n == next->first) {
-            n += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += n;
-                return;
-            }
-        }
-        free_[off] = n;
-    }
-    uint64_t used() const { return used_; }
-
-  private:
-    std::map<uint64_t, uint64_t> free_;   // offset -> bytes
-    std::map<uint64_t, uint64_t> sizes_;  // allocated offset -> bytes
-    uint64_t used_ = 0;
-};
+using rk::Arena;
 
 struct Request {
     uint64_t id = 0;
@@ -324,12 +275,15 @@ extern "C" int rk_server_create(const rk_tableset *ts, const rk_server_opts *opt
         delete s;
         return RK_ECUDA;
     }
-    if (cudaMalloc(&s->arena_mem, o.mem_cap) != cudaSuccess) {
+    // whole granules, so that every text up to max_text_len (<= mem_cap)
+    // fits in the empty arena
+    const uint64_t arena_bytes = Arena::round_up(o.mem_cap);
+    if (cudaMalloc(&s->arena_mem, arena_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return RK_ENOMEM;
     }
-    s->arena.reset(o.mem_cap);
+    s->arena.reset(arena_bytes);
     int rc = RK_OK;
     if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = RK_ECUDA;
