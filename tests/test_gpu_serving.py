@@ -97,3 +97,23 @@ def test_submit_rejects_bad_requests(tableset):
             assert rc == rk.RK_EINVAL
     finally:
         rk.rk_server_destroy(s)
+
+
+def test_text_of_mem_cap_bytes_is_admitted(tables, tableset):
+    """A cap off the 256-byte granule still admits a text of exactly cap
+    bytes, and an empty text (a granule of its own), one after the other."""
+    cap = (1 << 16) + 100
+    reqs = serving_texts(13, 1, tables, min_len=cap, max_len=cap)
+    tid, text = reqs[0]
+    text = np.resize(text, cap)
+    s = rk.rk_server_create(tableset, mem_cap=cap, max_text_len=cap)
+    try:
+        rid = rk.rk_server_submit(s, tid, text, cap)
+        rid0 = rk.rk_server_submit(s, tid, np.zeros(0, np.uint8), 0)
+        rc, keys, _ = rk.rk_server_take(s, rid, timeout_ms=20000)
+        assert rc == rk.RK_OK, rk.strerror(rc)
+        assert np.array_equal(keys, expect(tables, tid, text))
+        rc, keys, _ = rk.rk_server_take(s, rid0, timeout_ms=20000)
+        assert rc == rk.RK_OK and keys.size == 0
+    finally:
+        rk.rk_server_destroy(s)
