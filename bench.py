@@ -322,7 +322,7 @@ def measure_serving(torch, rk, dev, n_req=200, loads=(0.5, 1.0, 2.0, 4.0, 8.0), 
 
     def plain(tid, h):
         rc, cnt = rk.rk_search(tabs[tid], h, h.numel(), hkeys, hkeys.numel())
-        return cnt
+        return rc
 
     try:
         for tid, h in pinned[:4]:
@@ -357,23 +357,22 @@ def measure_serving(torch, rk, dev, n_req=200, loads=(0.5, 1.0, 2.0, 4.0, 8.0), 
                         pass
                     tid, h = pinned[i]
                     ids.append(rk.rk_server_submit(srv, tid, h, h.numel()))
-                lat, first, last = [], None, 0.0
+                lat, first, last, failed = [], None, 0.0, 0
                 for rid in ids:
                     rc, _, tm = rk.rk_server_take(srv, rid, timeout_ms=120000, key_cap=1 << 22)
+                    failed += rc != rk.RK_OK
                     lat.append(tm["done_us"] - tm["arrive_us"])
                     first = tm["arrive_us"] if first is None else min(first, tm["arrive_us"])
                     last = max(last, tm["done_us"])
                 nbytes = sum(pinned[i][1].numel() for i in picks)
                 # plain per-request calls, one at a time in arrival order
                 start = time.perf_counter()
-                plat, busy_until = [], 0.0
+                plat, plain_failed = [], 0
                 for at, i in zip(arrivals, picks):
-                    now = time.perf_counter() - start
-                    if now < at:
-                        while time.perf_counter() - start < at:
-                            pass
+                    while time.perf_counter() - start < at:
+                        pass
                     tid, h = pinned[i]
-                    plain(tid, h)
+                    plain_failed += plain(tid, h) != rk.RK_OK
                     plat.append((time.perf_counter() - start - at) * 1e6)
                 plain_span = time.perf_counter() - start - arrivals[0]
                 levels.append({
@@ -384,6 +383,7 @@ def measure_serving(torch, rk, dev, n_req=200, loads=(0.5, 1.0, 2.0, 4.0, 8.0), 
                     "plain_gbps": nbytes / plain_span / 1e9,
                     "plain_p50_ms": float(np.percentile(plat, 50)) / 1e3,
                     "plain_p99_ms": float(np.percentile(plat, 99)) / 1e3,
+                    "failed": failed, "plain_failed": plain_failed,
                 })
             stats = rk.rk_server_stats(srv)
         finally:
