@@ -656,7 +656,9 @@ def run_ours(args, rank, world, local_rank):
         slices = cpu_slices(w.text, lmax, CPU_SAMPLE_PER_CORE, cores)
         wall = time_oracle(pool, slices, w.patterns)
         pool.close()
+        one_s, _ = _oracle_slice((slices[0], w.patterns))  # one core, in this process
         cpu = {"value": cores * CPU_SAMPLE_PER_CORE / wall / 1e9, "unit": UNIT, "cores": cores,
+               "value_one_core": CPU_SAMPLE_PER_CORE / one_s / 1e9,
                "kind": "oracle",
                "sample": f"{cores} slices of {CPU_SAMPLE_PER_CORE} bytes (one per core) at random "
                          f"offsets of the 1 GiB text, all 100 patterns; {SLICE_HALO_NOTE}"}
