@@ -45,7 +45,12 @@
 /* (a * b) mod p through a full 128-bit product. */
 uint64_t oracle_mulmod(uint64_t a, uint64_t b) {
     unsigned __int128 prod = (unsigned __int128)(a % ORACLE_P) * (unsigned __int128)(b % ORACLE_P);
+#if ORACLE_MUTANT == 8
+    /* mutant: one Mersenne fold, no final conditional subtract */
+    return (uint64_t)(prod & ORACLE_P) + (uint64_t)(prod >> 61);
+#else
     return (uint64_t)(prod % ORACLE_P);
+#endif
 }
 
 static uint64_t addmod(uint64_t a, uint64_t b) { /* a, b < p */
@@ -234,7 +239,11 @@ int64_t oracle_rabin_karp(const uint8_t *T, uint64_t n, const uint8_t *P, const 
         for (uint64_t x = 0; x < nwin; ++x) {
             if (x > 0) {
                 hy = submod(hy, oracle_mulmod((uint64_t)T[x - 1], top));
+#if ORACLE_MUTANT == 7
+                hy = addmod(oracle_mulmod(hy, base), (uint64_t)T[x - 2 + L]); /* mutant: incoming byte one early */
+#else
                 hy = addmod(oracle_mulmod(hy, base), (uint64_t)T[x - 1 + L]);
+#endif
             }
             for (uint64_t i = lower_bound(tab, cnt, hy); i < cnt && tab[i].h == hy; ++i) {
                 uint32_t p = tab[i].pid;
@@ -256,6 +265,9 @@ int64_t oracle_rabin_karp(const uint8_t *T, uint64_t n, const uint8_t *P, const 
                 ms[mcount].pid = p;
                 ms[mcount].off = x;
                 ++mcount;
+#if ORACLE_MUTANT == 6
+                break; /* mutant: one pattern id per hash value (duplicates collapsed) */
+#endif
             }
         }
     }

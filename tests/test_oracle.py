@@ -25,8 +25,11 @@ def test_hand_examples_parse():
 #   2 reports hash equality without comparing bytes,
 #   3 removes the outgoing byte with B^L instead of B^(L-1),
 #   4 never compares a pattern's last byte,
-#   5 hashes the bytes in reverse order.
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5])
+#   5 hashes the bytes in reverse order,
+#   6 reports one pattern id per hash value (duplicate patterns collapsed),
+#   7 takes the rolling update's incoming byte one position early,
+#   8 reduces a product mod 2^61 - 1 by one fold without the final subtract.
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_pins_catch_mutant(mutant):
     failed = []
     for check in oracle_pins.ALL_CHECKS:
