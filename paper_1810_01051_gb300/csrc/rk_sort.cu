@@ -521,19 +521,20 @@ uint32_t bits_for(uint64_t max_value) {
 // CTAs of the fused sort: at most two per SM, all resident (0: the kernel
 // does not fit on this device).
 uint32_t fused_grid(int sm_count) {
+    constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int dev_seen[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
-    static uint32_t per_sm[8];
+    static bool dev_seen[kMaxDevices] = {};
+    static uint32_t per_sm[kMaxDevices];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 8) return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
     std::lock_guard<std::mutex> lk(mu);
-    if (dev_seen[dev] != dev) {
+    if (!dev_seen[dev]) {
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rk_sort_fused_kernel, kThreads, 0) !=
             cudaSuccess)
             nb = 0;
         per_sm[dev] = (uint32_t)std::max(0, std::min(nb, 2));
-        dev_seen[dev] = dev;
+        dev_seen[dev] = true;
     }
     return per_sm[dev] * (uint32_t)sm_count;
 }
