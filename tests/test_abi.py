@@ -127,3 +127,20 @@ def test_handle_entry_points_reject_null(lib):
     lib.rk_batch_destroy(None)
     lib.rk_tableset_destroy(None)
     lib.rk_server_destroy(None)
+
+
+def test_binding_types_match_header(lib):
+    # every declared function has argument types in the binding and the
+    # header's return type (a uint64_t left as the ctypes default int would
+    # be truncated)
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "rk.h")).read(), flags=re.S)
+    decl = {m.group(2): m.group(1).strip()
+            for m in re.finditer(r"\b((?:const\s+)?\w+\s*\*?)\s*(rk_\w+)\s*\(", src)}
+    want = {"int": ctypes.c_int, "uint64_t": ctypes.c_uint64, "void": None,
+            "const char *": ctypes.c_char_p}
+    assert set(decl) == set(rk.EXPORTS)
+    for name, ret in decl.items():
+        f = getattr(lib, name)
+        assert ret in want, (name, ret)
+        assert f.restype == want[ret], (name, ret, f.restype)
+        assert f.argtypes is not None, name
