@@ -139,8 +139,13 @@ def test_binding_types_match_header(lib):
     want = {"int": ctypes.c_int, "uint64_t": ctypes.c_uint64, "void": None,
             "const char *": ctypes.c_char_p}
     assert set(decl) == set(rk.EXPORTS)
+    nparams = {}
+    for m in re.finditer(r"\b(rk_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = m.group(2).strip()
+        nparams[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
     for name, ret in decl.items():
         f = getattr(lib, name)
         assert ret in want, (name, ret)
         assert f.restype == want[ret], (name, ret, f.restype)
         assert f.argtypes is not None, name
+        assert len(f.argtypes) == nparams[name], (name, len(f.argtypes), nparams[name])
