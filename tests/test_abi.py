@@ -149,3 +149,38 @@ def test_binding_types_match_header(lib):
         assert f.restype == want[ret], (name, ret, f.restype)
         assert f.argtypes is not None, name
         assert len(f.argtypes) == nparams[name], (name, len(f.argtypes), nparams[name])
+
+
+# ctypes mirror of each C struct: (C name, binding class)
+STRUCTS = [("rk_build_opts", "BuildOpts"), ("rk_table_info", "TableInfo"),
+           ("rk_batch_opts", "BatchOpts"), ("rk_batch_info", "BatchInfo"),
+           ("rk_server_opts", "ServerOpts"), ("rk_request_times", "RequestTimes"),
+           ("rk_server_stats", "ServerStats")]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # a C program compiled against include/rk.h prints every struct's size and
+    # field offsets; the binding's ctypes structures must agree field by field
+    import shutil
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not found")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rk.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        cls = getattr(rk, pyname)
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-Wall", f"-I{os.path.join(ROOT, 'include')}", str(src),
+                    "-o", str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out.splitlines()}
+    for cname, pyname in STRUCTS:
+        cls = getattr(rk, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
