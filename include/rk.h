@@ -293,6 +293,7 @@ typedef struct rk_batch_info {
     uint32_t offset_bits, id_bits, item_bits;  /* key fields */
     uint32_t warps, tile_bytes, stages, ctas_per_sm, s2_in_smem, smem_bytes;
     uint32_t n_chunks, max_chunks;             /* work chunks of the current batch */
+    uint32_t n_items;                          /* items of the current batch */
 } rk_batch_info;
 
 /* A batch engine over a table set: device buffers for opts' limits and the
@@ -331,7 +332,8 @@ int rk_batch_results(const rk_batch *b, const uint64_t **d_keys, const uint64_t 
 
 /* Copy the results of the last run to host memory and wait: h_info[0..2)
  * (count, status); if the run succeeded and fit, h_item_offsets[0 .. n_items]
- * (may be NULL) and the first min(count, key_cap) keys (h_keys may be NULL).
+ * (n_items of the last rk_batch_set, also in rk_batch_info; NULL allowed) and
+ * the first min(count, key_cap) keys (h_keys may be NULL).
  * Errors: RK_EINVAL, RK_ECUDA.                                               */
 int rk_batch_read(const rk_batch *b, uint64_t *h_keys, uint64_t key_cap, uint64_t *h_item_offsets,
                   uint64_t *h_info, void *stream);

@@ -688,6 +688,7 @@ extern "C" int rk_batch_info_get(const rk_batch *b, rk_batch_info *info) {
     r.smem_bytes = b->smem;
     r.n_chunks = (uint32_t)b->h_chunks.size();
     r.max_chunks = b->max_chunks;
+    r.n_items = (uint32_t)b->h_items.size();
     *info = r;
     return RK_OK;
 }

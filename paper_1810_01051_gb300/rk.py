@@ -70,7 +70,7 @@ class BatchOpts(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "offset_bits", "id_bits", "item_bits", "warps", "tile_bytes", "stages", "ctas_per_sm",
-        "s2_in_smem", "smem_bytes", "n_chunks", "max_chunks")]
+        "s2_in_smem", "smem_bytes", "n_chunks", "max_chunks", "n_items")]
 
 
 class ServerOpts(ctypes.Structure):
@@ -403,6 +403,8 @@ def rk_batch_info(b: int) -> dict:
 def rk_batch_set(b: int, table_of_item: Sequence[int], d_texts: Sequence, text_lens: Sequence[int],
                  stream=None) -> None:
     n = len(table_of_item)
+    if len(d_texts) != n or len(text_lens) != n:
+        raise ValueError("rk_batch_set: one table index, text and length per item")
     tabs = np.asarray(table_of_item, dtype=np.uint32)
     ptrs = np.array([_ptr(t) for t in d_texts] or [0], dtype=np.uint64)
     lens = np.asarray(list(text_lens) or [0], dtype=np.uint64)
@@ -422,9 +424,14 @@ def rk_batch_results(b: int) -> Tuple[int, int, int]:
 
 
 def rk_batch_read(b: int, n_items: int, key_cap: int, stream=None):
-    """(count, status, keys uint64[min(count, key_cap)], offsets uint64[n_items+1])."""
+    """(count, status, keys uint64[min(count, key_cap)], offsets uint64[n_items+1]).
+    n_items must be the item count of the last rk_batch_set (the offsets
+    buffer is sized from the batch itself)."""
+    have = rk_batch_info(b)["n_items"]
+    if n_items != have:
+        raise ValueError(f"rk_batch_read: the batch holds {have} items, not {n_items}")
     keys = np.empty(max(key_cap, 1), dtype=np.uint64)
-    offs = np.zeros(n_items + 1, dtype=np.uint64)
+    offs = np.zeros(have + 1, dtype=np.uint64)
     info = np.zeros(2, dtype=np.uint64)
     _check(load().rk_batch_read(b, keys.ctypes.data, key_cap, offs.ctypes.data,
                                 info.ctypes.data, _stream(stream)), "rk_batch_read")
