@@ -200,6 +200,33 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take the address of {type(x)!r}")
 
 
+def _buf(x, need: int, what: str, device: bool) -> int:
+    """Address of a buffer argument, after the checks the binding can make: a
+    tensor or array must be contiguous, hold `need` bytes and live where the
+    call reads it (device memory for the d_ arguments, host memory for the h_
+    ones: a host address handed to a kernel would fault the GPU).  A raw
+    integer address is passed through, as the C contract allows."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if bool(x.is_cuda) != device:
+            raise RkError(RK_EINVAL, f"{what}: a {'CUDA' if device else 'host'} tensor is required")
+        if not x.is_contiguous():
+            raise RkError(RK_EINVAL, f"{what}: not contiguous")
+        have = x.numel() * x.element_size()
+    elif isinstance(x, np.ndarray):
+        if device:
+            raise RkError(RK_EINVAL, f"{what}: a numpy array is host memory")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise RkError(RK_EINVAL, f"{what}: not contiguous")
+        have = x.nbytes
+    else:
+        return _ptr(x)
+    if have < need:
+        raise RkError(RK_EINVAL, f"{what}: {have} bytes, the call needs {need}")
+    return _ptr(x)
+
+
 def _stream(stream) -> int:
     if stream is None:
         return 0
@@ -273,7 +300,9 @@ def rk_sort_launches(table: int, n: int, capacity: int) -> int:
 
 def rk_scan_device(table: int, d_text, n: int, d_keys, capacity: int, d_info,
                    stream=None) -> None:
-    _check(load().rk_scan_device(table, _ptr(d_text), n, _ptr(d_keys), capacity, _ptr(d_info),
+    _check(load().rk_scan_device(table, _buf(d_text, n, "d_text", True), n,
+                                 _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                 _buf(d_info, 16, "d_info", True),
                                  _stream(stream)), "rk_scan_device")
 
 
@@ -294,22 +323,30 @@ def rk_scan_launches(table: int, n: int, workspace_bytes: int) -> int:
 def rk_scan_device_ws(table: int, d_text, n: int, d_keys, capacity: int, d_info, d_workspace,
                       workspace_bytes: int, stream=None) -> None:
     """rk_scan_device with the survivors verified by a second kernel."""
-    _check(load().rk_scan_device_ws(table, _ptr(d_text), n, _ptr(d_keys), capacity, _ptr(d_info),
-                                    _ptr(d_workspace), workspace_bytes, _stream(stream)),
+    _check(load().rk_scan_device_ws(table, _buf(d_text, n, "d_text", True), n,
+                                    _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                    _buf(d_info, 16, "d_info", True),
+                                    _buf(d_workspace, workspace_bytes, "d_workspace", True),
+                                    workspace_bytes, _stream(stream)),
            "rk_scan_device_ws")
 
 
 def rk_sort_device(table: int, n: int, d_keys, capacity: int, d_info, d_workspace,
                    workspace_bytes: int, stream=None) -> None:
-    _check(load().rk_sort_device(table, n, _ptr(d_keys), capacity, _ptr(d_info),
-                                 _ptr(d_workspace), workspace_bytes, _stream(stream)),
+    _check(load().rk_sort_device(table, n, _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                 _buf(d_info, 16, "d_info", True),
+                                 _buf(d_workspace, workspace_bytes, "d_workspace", True),
+                                 workspace_bytes, _stream(stream)),
            "rk_sort_device")
 
 
 def rk_search_device(table: int, d_text, n: int, d_keys, capacity: int, d_info, d_workspace,
                      workspace_bytes: int, stream=None) -> None:
-    _check(load().rk_search_device(table, _ptr(d_text), n, _ptr(d_keys), capacity, _ptr(d_info),
-                                   _ptr(d_workspace), workspace_bytes, _stream(stream)),
+    _check(load().rk_search_device(table, _buf(d_text, n, "d_text", True), n,
+                                   _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                   _buf(d_info, 16, "d_info", True),
+                                   _buf(d_workspace, workspace_bytes, "d_workspace", True),
+                                   workspace_bytes, _stream(stream)),
            "rk_search_device")
 
 
@@ -317,7 +354,8 @@ def rk_search(table: int, h_text, n: int, h_keys, capacity: int) -> Tuple[int, i
     """Host-buffer search.  Returns (status, n_matches); RK_ECAPACITY is
     returned, not raised, so the caller can retry with the reported count."""
     cnt = ctypes.c_uint64(0)
-    rc = load().rk_search(table, _ptr(h_text), n, _ptr(h_keys), capacity, ctypes.byref(cnt))
+    rc = load().rk_search(table, _buf(h_text, n, "h_text", False), n,
+                          _buf(h_keys, 8 * capacity, "h_keys", False), capacity, ctypes.byref(cnt))
     if rc not in (RK_OK, RK_ECAPACITY):
         raise RkError(rc, "rk_search")
     return rc, int(cnt.value)
@@ -325,7 +363,9 @@ def rk_search(table: int, h_text, n: int, h_keys, capacity: int) -> Tuple[int, i
 
 def rk_window_hashes_device(d_text, n: int, L: int, base_log2: int, d_hashes,
                             stream=None) -> None:
-    _check(load().rk_window_hashes_device(_ptr(d_text), n, L, base_log2, _ptr(d_hashes),
+    windows = n - L + 1 if 1 <= L <= n else 0
+    _check(load().rk_window_hashes_device(_buf(d_text, n if windows else 0, "d_text", True), n, L,
+                                          base_log2, _buf(d_hashes, 8 * windows, "d_hashes", True),
                                           _stream(stream)), "rk_window_hashes_device")
 
 
@@ -334,8 +374,9 @@ def rk_search_device_noalloc(table: int, d_text, n: int, d_keys, capacity: int, 
     """rk_search_device for callers that cannot allocate: the sort's scratch is
     a fixed array inside the library (capacity <= RK_NOALLOC_MAX_KEYS); calls
     that overlap on the GPU race on it."""
-    _check(load().rk_search_device_noalloc(table, _ptr(d_text), n, _ptr(d_keys), capacity,
-                                           _ptr(d_info), _stream(stream)),
+    _check(load().rk_search_device_noalloc(table, _buf(d_text, n, "d_text", True), n,
+                                           _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                           _buf(d_info, 16, "d_info", True), _stream(stream)),
            "rk_search_device_noalloc")
 
 
@@ -343,8 +384,10 @@ def rk_debug_scan_withheld(table: int, d_text, n: int, d_keys, capacity: int, d_
                            timeout_ms: int, stream=None) -> None:
     """Failure-detection diagnostics: a scan whose copies never arrive, so its
     bounded waits run out and d_info[1] becomes RK_ETIMEOUT."""
-    _check(load().rk_debug_scan_withheld(table, _ptr(d_text), n, _ptr(d_keys), capacity,
-                                         _ptr(d_info), timeout_ms, _stream(stream)),
+    _check(load().rk_debug_scan_withheld(table, _buf(d_text, n, "d_text", True), n,
+                                         _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                         _buf(d_info, 16, "d_info", True), timeout_ms,
+                                         _stream(stream)),
            "rk_debug_scan_withheld")
 
 
@@ -353,8 +396,9 @@ def rk_paper_search_device(d_text, n: int, pattern: bytes, d_result, threads_per
     """The paper's one-thread-per-offset matcher for one pattern; d_result[x] = 1
     where a match starts."""
     pat = np.frombuffer(bytes(pattern), dtype=np.uint8).copy()
-    _check(load().rk_paper_search_device(_ptr(d_text) if n else None, n, pat.ctypes.data,
-                                         len(pattern), _ptr(d_result) if n else None,
+    _check(load().rk_paper_search_device(_buf(d_text, n, "d_text", True) if n else None, n,
+                                         pat.ctypes.data, len(pattern),
+                                         _buf(d_result, n, "d_result", True) if n else None,
                                          threads_per_block, _stream(stream)),
            "rk_paper_search_device")
 
@@ -406,7 +450,8 @@ def rk_batch_set(b: int, table_of_item: Sequence[int], d_texts: Sequence, text_l
     if len(d_texts) != n or len(text_lens) != n:
         raise ValueError("rk_batch_set: one table index, text and length per item")
     tabs = np.asarray(table_of_item, dtype=np.uint32)
-    ptrs = np.array([_ptr(t) for t in d_texts] or [0], dtype=np.uint64)
+    ptrs = np.array([_buf(t, int(L), "d_texts", True) for t, L in zip(d_texts, text_lens)]
+                    or [0], dtype=np.uint64)
     lens = np.asarray(list(text_lens) or [0], dtype=np.uint64)
     _check(load().rk_batch_set(b, n, tabs.ctypes.data if n else None, ptrs.ctypes.data,
                                lens.ctypes.data, _stream(stream)), "rk_batch_set")
@@ -463,7 +508,8 @@ def rk_server_destroy(s: int) -> None:
 def rk_server_submit(s: int, table: int, h_text, n: int) -> int:
     """The host buffer must stay alive and unchanged until the request is taken."""
     rid = ctypes.c_uint64(0)
-    _check(load().rk_server_submit(s, table, _ptr(h_text) if n else None, n, ctypes.byref(rid)),
+    _check(load().rk_server_submit(s, table, _buf(h_text, n, "h_text", False) if n else None, n,
+                                   ctypes.byref(rid)),
            "rk_server_submit")
     return int(rid.value)
 

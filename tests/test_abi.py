@@ -184,3 +184,32 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_binding_refuses_buffers_a_call_cannot_use(lib):
+    # refused in the binding, before any CUDA call (null table handles, so a
+    # check that let a buffer through would still end in RK_EINVAL, not a
+    # crash; the message tells which refused): host memory where the call
+    # reads device memory (a kernel would fault on it), too few bytes for what
+    # the call touches, non-contiguous views
+    torch = pytest.importorskip("torch")
+    host_t = torch.zeros(64, dtype=torch.int64)
+    info = torch.zeros(2, dtype=torch.int64)
+    arr = np.zeros(64, dtype=np.uint64)
+    cases = [
+        (lambda: rk.rk_scan_device(0, 0, 0, host_t, 64, 0), "CUDA tensor is required"),
+        (lambda: rk.rk_search_device(0, 0, 0, arr, 64, 0, 0, 0), "numpy array is host memory"),
+        (lambda: rk.rk_sort_device(0, 10, 0, 0, info, 0, 0), "CUDA tensor is required"),
+        (lambda: rk.rk_search(0, np.zeros(10, np.uint8), 10, arr, 65), "bytes, the call needs"),
+        (lambda: rk.rk_search(0, np.zeros(20, np.uint8)[::2], 10, arr, 8), "not contiguous"),
+        (lambda: rk.rk_window_hashes_device(host_t, 100, 4, 8, 0), "CUDA tensor is required"),
+        (lambda: rk.rk_paper_search_device(0, 16, b"ab", arr), "numpy array is host memory"),
+    ]
+    for call, why in cases:
+        with pytest.raises(rk.RkError) as e:
+            call()
+        assert e.value.code == rk.RK_EINVAL and why in str(e.value), (why, str(e.value))
+    # raw addresses pass through to the library, which checks what it can
+    with pytest.raises(rk.RkError) as e:
+        rk.rk_scan_device(0, 0, 0, 0, 0, 0)
+    assert e.value.code == rk.RK_EINVAL and "rk_scan_device" in str(e.value)
