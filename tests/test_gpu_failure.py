@@ -4,7 +4,6 @@ RK_ETIMEOUT in the device header, and leave the context usable."""
 
 import time
 
-import numpy as np
 import pytest
 
 import oracle

@@ -7,7 +7,6 @@ import inspect
 import os
 
 import numpy as np
-import pytest
 
 import workloads
 from workloads import gen
