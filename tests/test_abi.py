@@ -213,3 +213,30 @@ def test_binding_refuses_buffers_a_call_cannot_use(lib):
     with pytest.raises(rk.RkError) as e:
         rk.rk_scan_device(0, 0, 0, 0, 0, 0)
     assert e.value.code == rk.RK_EINVAL and "rk_scan_device" in str(e.value)
+
+
+def compile_c_example(tmp_path):
+    """tests/c_api_example.c compiled and linked against include/rk.h and
+    librk.so, as a C user would (returns the executable's path)."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not found")
+    build_lib.build()
+    lib_dir = os.path.dirname(build_lib.LIB)
+    exe = tmp_path / "c_api_example"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}",
+                    os.path.join(ROOT, "tests", "c_api_example.c"), f"-L{lib_dir}", "-lrk",
+                    f"-Wl,-rpath,{lib_dir}", "-o", str(exe)], check=True, capture_output=True,
+                   text=True)
+    return str(exe)
+
+
+def test_c_example_builds_and_fails_cleanly_without_a_device(tmp_path):
+    exe = compile_c_example(tmp_path)
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: tests/test_gpu_search.py runs the example")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    # no device: the status comes back as RK_ECUDA, nothing aborts
+    assert r.returncode == 1 and "rk_build: CUDA error" in r.stderr, (r.returncode, r.stderr)

@@ -217,3 +217,18 @@ def test_matcher_wrapper():
         assert m.search(torch.zeros(0, dtype=torch.uint8, device="cuda")).numel() == 0
     finally:
         m.close()
+
+
+def test_c_example_program(tmp_path):
+    """The C example (tests/c_api_example.c) built against the header and
+    library prints the oracle's list."""
+    import subprocess
+    from test_abi import compile_c_example
+    exe = compile_c_example(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    text = np.frombuffer(b"xxGATTACAxACGTxxGATTACA", np.uint8)
+    ids, offs = oracle.bruteforce(text, [b"GATTACA", b"ACGT"])
+    expect = [f"{i} {o}" for i, o in zip(ids.tolist(), offs.tolist())]
+    assert expect == ["0 2", "0 16", "1 10"]
+    assert r.stdout.split("\n")[:-1] == expect
