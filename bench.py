@@ -615,7 +615,9 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
 
     extra = {}
-    if rank == 0 and not args.no_extras:
+    # the extra workloads are single-GPU measurements: at N > 1 the other ranks
+    # would wait for them inside the max-over-ranks collective
+    if rank == 0 and world == 1 and not args.no_extras:
         for name, fn in (("batched", lambda: measure_batched(torch, rk, dev, 2 << 20)),
                          ("served", lambda: measure_serving(torch, rk, dev)),
                          ("paper_kernel", lambda: measure_paper_kernel(torch, rk, dev)),
