@@ -39,8 +39,9 @@ UNIT = "GB/s"
 WORKLOAD = "zipf_text_1GiB_100_patterns_len4-32_density1e-6"
 # the sources the scan kernel is compiled from (the profile records their hash)
 SCAN_SRCS = [os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", f)
-             for f in ("rk_scan.cu", "rk_scan_body.cuh", "rk_layout.cuh", "rk_internal.cuh",
-                       "rk_verify.cu", "rk_sortws.cuh")]
+             for f in ("rk_scan.cu", "rk_scan_kernel.cuh", "rk_scan_k_role.cu", "rk_scan_body.cuh",
+                       "rk_layout.cuh", "rk_internal.cuh", "rk_verify.cu", "rk_sortws.cuh",
+                       "rk_table.cu")]
 PROFILE = os.path.join(ROOT, "profiles", "rk_scan_zipf_1GiB.md")
 CPU_SAMPLE_PER_CORE = 8 << 20   # bytes per core for the oracle baseline
 SLICE_HALO_NOTE = "each slice carries (longest pattern - 1) extra bytes"

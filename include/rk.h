@@ -82,10 +82,24 @@ typedef struct rk_build_opts {
                                   (default 49152) */
     uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */
     uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
-    uint32_t sample;           /* 0: when every pattern has >= 7 bytes, scans with a candidate
-                                  list (rk_scan_device_ws) test every 4th window position
-                                  against the patterns' 4-byte grams at offsets 0..3;
-                                  1: every position against the prefixes */
+    uint32_t sample;           /* 0: when every pattern has >= 7 bytes and no role filter is
+                                  built, scans with a candidate list (rk_scan_device_ws) test
+                                  every 4th window position against the patterns' 4-byte
+                                  grams at offsets 0..3; 1: every position against the
+                                  prefixes */
+    uint32_t role_step;        /* role filter (see below): 0 = the builder's choice (with
+                                  filter RK_FILTER_AUTO; none with a forced filter), 1 = none,
+                                  2 or 4 = that sampling step when the patterns allow it.
+                                  A role filter tests every 2nd or 4th text position p with
+                                  the 4 bytes at p: those bytes stand for the pattern bytes
+                                  j..j+3 of a window starting at p - j, either on their own
+                                  (shorter patterns) or together with the 4 bytes at p + 4
+                                  (the pattern bytes j+4..j+7).  Step 4 needs every pattern
+                                  to have at least 7 bytes, step 2 at least 4 (at most 64
+                                  patterns of 4 bytes); the builder also declines a set with
+                                  more than one gram per 64 bits of the filter's largest
+                                  size (2^19 bits), where the other filters pass fewer
+                                  windows.  Every scan of the table uses it. */
 } rk_build_opts;
 
 /* Read-back of a table's shape and launch configuration. */
@@ -102,6 +116,9 @@ typedef struct rk_table_info {
     uint64_t device_bytes;     /* device memory held by the table */
     uint32_t sample_step;      /* 4: sampled stage 1 available (see rk_build_opts.sample), else 1 */
     uint32_t sample_filter_log2_bits;  /* its bit set's size (0 without) */
+    uint32_t role_step;        /* 2 or 4: the scans use a role filter (rk_build_opts.role_step);
+                                  0: none */
+    uint32_t role_filter_log2_bits;    /* its bit set's size (0 without) */
 } rk_table_info;
 
 /* Human-readable text of a status code (static storage). */

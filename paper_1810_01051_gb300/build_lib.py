@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "librk.so")
 
-SOURCES = ["rk_table.cu", "rk_scan.cu", "rk_sort.cu", "rk_api.cu", "rk_noalloc.cu",
+SOURCES = ["rk_table.cu", "rk_scan.cu", "rk_scan_k_none.cu", "rk_scan_k_repl.cu",
+           "rk_scan_k_flat.cu", "rk_scan_k_role.cu", "rk_sort.cu", "rk_api.cu", "rk_noalloc.cu",
            "rk_batch.cu", "rk_server.cu", "rk_paper.cu", "rk_verify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

@@ -347,8 +347,9 @@ extern "C" int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, con
     for (uint32_t i = 0; i < n_tables; ++i) {
         const uint32_t k = patterns_per_table[i];
         if (k > RK_MAX_PATTERNS) { delete ts; return RK_EINVAL; }
+        // table sets are scanned unsampled, with the prefix filter
         int rc = build_blob(patterns + byte_off, lens + pat_off, k, base_log2, filt,
-                            o.filter_log2_bits, 1, &blobs[i]);  // table sets are scanned unsampled
+                            o.filter_log2_bits, 1, 1, &blobs[i]);
         if (rc) { delete ts; return rc; }
         for (uint32_t j = 0; j < k; ++j) byte_off += lens[pat_off + j];
         pat_off += k;

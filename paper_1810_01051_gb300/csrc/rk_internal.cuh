@@ -18,6 +18,7 @@ constexpr uint64_t kP61 = (1ull << 61) - 1;
 constexpr uint32_t kFilterMult = 0x85EBCA77u;
 constexpr uint32_t kGramMult = 0x9E3779B1u;
 constexpr uint64_t kGroupMult = 0x9E3779B97F4A7C15ull;
+constexpr uint32_t kRoleMult = 0x9E3779B1u;
 
 enum FilterMode : uint32_t { kFilterNone = 0, kFilterReplicated = 1, kFilterFlat = 2 };
 
@@ -88,6 +89,22 @@ struct DevTable {
     const SampSlot *smap;     // 2^smap_bits slots (in the survivor-stage tables)
     uint32_t smap_bits;
 
+    // Role filter (rf_step 2 or 4; 0: none): stage 1 tests only positions p
+    // that are multiples of rf_step, with the 4-byte gram G(p) = T[p..p+4)
+    // read as a little-endian word.  The pattern grams at offsets j <
+    // rf_step set role bits in a flat bit set: S, a gram that makes window
+    // p - j a candidate on its own; L, a gram whose pattern continues with
+    // the gram at offset j + 4; B, such a continuation.  Window p - j is a
+    // candidate when G(p) has role S, or role L and G(p + 4) role B.  A word
+    // of the bit set is chosen by the top bits of lo = G * kRoleMult, and
+    // role i of G sits at bit (lo + 31 - i) mod 32 of it, so a rotation by
+    // lo brings the roles to bits 31, 30, 29; S also sets bit 28 (both S
+    // bits are tested).
+    uint32_t rf_step;
+    const uint32_t *rfilter;  // the bit set's shared-memory image
+    uint32_t rfilter_bytes;
+    uint32_t rf_shift;        // byte address of G's word: (lo >> rf_shift) & ~3
+
     uint32_t n_patterns;
     uint32_t lmin, lmax;
     uint32_t base_log2;
@@ -120,6 +137,7 @@ struct rk_table {
     uint32_t n_grams = 0;
     uint32_t filter_log2_bits = 0;
     uint32_t sfilter_log2_bits = 0;
+    uint32_t rfilter_log2_bits = 0;
     uint32_t filter_opt = RK_FILTER_AUTO;
     void *d_mem = nullptr;
     size_t d_bytes = 0;
@@ -157,15 +175,18 @@ namespace rk {
 struct TableBlob {
     std::vector<uint8_t> bytes;
     size_t o_filter = 0, o_grams = 0, o_glens = 0, o_ghdr = 0, o_slots = 0, o_gpids = 0,
-           o_pbytes = 0, o_poff = 0, o_plen = 0, o_lens = 0, o_sfilter = 0, o_smap = 0;
+           o_pbytes = 0, o_poff = 0, o_plen = 0, o_lens = 0, o_sfilter = 0, o_smap = 0,
+           o_rfilter = 0;
     DevTable meta{};
-    uint32_t n_grams = 0, filter_log2_bits = 0, sfilter_log2_bits = 0;
+    uint32_t n_grams = 0, filter_log2_bits = 0, sfilter_log2_bits = 0, rfilter_log2_bits = 0;
 };
 
-// sample_opt: rk_build_opts.sample (1: no sampled structures).
+// sample_opt: rk_build_opts.sample (1: no sampled structures); role_opt:
+// rk_build_opts.role_step (0: chosen by the builder, 1: no role filter, 2 or
+// 4: that step if the patterns allow it).
 int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
                uint32_t filter_opt, uint32_t filter_bits_opt, uint32_t sample_opt,
-               TableBlob *out);
+               uint32_t role_opt, TableBlob *out);
 void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dev_base);
 
 // Candidate list of a scan whose survivors are verified in a second pass

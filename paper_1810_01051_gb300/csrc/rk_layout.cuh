@@ -12,7 +12,7 @@ constexpr uint32_t kMatchCap = 128;           // buffered match keys per warp
 constexpr uint32_t kStagePad = 16;            // readable slack after each staged tile
 
 struct SmemLayout {
-    uint32_t filter_off, s2_off, bar_off, queue_off, mcount_off, match_off, stage_off;
+    uint32_t filter_off, s2_off, bar_off, queue_off, mcount_off, qcount_off, match_off, stage_off;
     uint32_t stage_stride;
     uint32_t total;
 };
@@ -37,6 +37,8 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t filter_bytes, uint32_
     L.queue_off = off;
     off = align_up(off + warps * kQueueCap * 2, 16);
     L.mcount_off = off;
+    off = align_up(off + warps * 4, 16);
+    L.qcount_off = off;
     off = align_up(off + warps * 4, 16);
     L.match_off = off;
     off = align_up(off + warps * kMatchCap * 8, 128);

@@ -586,4 +586,211 @@ __device__ __forceinline__ void consume_tile_s4(const WinCtx &C, const WarpCtx &
     cand_flush(C, w, cc, buf, u0, lane);
 }
 
+// ------------------------------------------------------------ role filter
+// Stage 1 with a role filter (DevTable::rf_step): only every STEP-th
+// position p is looked up, with its gram G(p) (4 bytes, little-endian).
+
+// G's word of the bit set, rotated so that G's roles S, L, B sit at bits
+// 31, 30, 29.
+__device__ __forceinline__ uint32_t rf_probe(uint32_t g, const uint8_t *rfilt, uint32_t rshift) {
+    const uint32_t lo = g * kRoleMult;
+    const uint32_t word = *reinterpret_cast<const uint32_t *>(rfilt + ((lo >> rshift) & ~3u));
+    return __funnelshift_r(word, word, lo);
+}
+
+// Roles of the sampled positions of one 16-byte chunk (words v; v4: the next
+// chunk's first word), one nibble per position i (bit 3 S, bit 2 L, bit 1 B,
+// bit 0 S's second bit):
+//   STEP 2: positions 2i, i < 8, in nibble 7 - i of the 32-bit result;
+//   STEP 4: positions 4i, i < 4, in nibble 3 - i of the low 16 bits.
+template <int STEP>
+__device__ __forceinline__ uint32_t rf_chunk(const uint4 v, uint32_t v4, const uint8_t *rfilt,
+                                             uint32_t rshift) {
+    const uint32_t wd[5] = {v.x, v.y, v.z, v.w, v4};
+    uint32_t a = 0, b = 0;  // two independent accumulators
+    if constexpr (STEP == 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t g =
+                (i & 1) ? __funnelshift_r(wd[i >> 1], wd[(i >> 1) + 1], 16) : wd[i >> 1];
+            const uint32_t r = rf_probe(g, rfilt, rshift);
+            if (i < 4) a = __funnelshift_l(r, a, 4);  // a = a << 4 | r >> 28
+            else b = __funnelshift_l(r, b, 4);
+        }
+        return __byte_perm(b, a, 0x5410);  // a << 16 | b
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t r = rf_probe(wd[i], rfilt, rshift);
+            if (i < 2) a = __funnelshift_l(r, a, 4);
+            else b = __funnelshift_l(r, b, 4);
+        }
+        return (a << 8) | b;
+    }
+}
+
+// Candidate positions of a chunk from its role nibbles and the next chunk's
+// (whose first positions hold the second grams of the last ones): bit 0 of
+// nibble 7 - i is set when sampled position i of the chunk makes its windows
+// candidates: both S bits, or L with B at the position 4 bytes on.
+template <int STEP>
+__device__ __forceinline__ uint32_t rf_cands(uint32_t acc, uint32_t accn) {
+    uint32_t x, comb, keep;
+    if constexpr (STEP == 2) {
+        x = acc;
+        comb = __funnelshift_l(accn, acc, 9);  // B of position i + 2 under L of i
+        keep = 0x11111111u;
+    } else {
+        x = __byte_perm(accn, acc, 0x5410);    // acc << 16 | accn
+        comb = x << 5;                         // B of position i + 1 under L of i
+        keep = 0x11110000u;
+    }
+    return ((x & (x >> 3)) | ((x & comb) >> 2)) & keep;
+}
+
+// A lane's candidates of one round in one word: the mask of its chunk k
+// (bits 4n) shifted left by k, so bit b belongs to chunk b mod 4, position
+// 7 - b / 4 of it.  Buffer position of the sampled position named by bit b,
+// for the lane's first chunk cbase (its chunk k is cbase + 32k).
+template <int STEP>
+__device__ __forceinline__ uint32_t rf_pos(uint32_t cbase, uint32_t b) {
+    return 16u * (cbase + 32u * (b & 3u)) + (uint32_t)STEP * (7u - (b >> 2));
+}
+
+// The windows a sampled position pos stands for: pos - j, j < STEP, those
+// that start in this tile ([0, tile); windows before it belong to the
+// previous tile).  DEFER: stage 2a, candidates to the list; else stage 2.
+template <int STEP, int MODE, bool DEFER>
+__device__ __forceinline__ void rf_windows(const WinCtx &C, const WarpCtx &w, const CandList *cc,
+                                           const uint8_t *buf, uint32_t pos, uint64_t u0,
+                                           uint32_t tile) {
+#pragma unroll 1
+    for (uint32_t j = 0; j < (uint32_t)STEP; ++j) {
+        if (pos < j || pos - j >= tile) continue;
+        if (DEFER) cand_window(C, w, *cc, buf, pos - j, u0);
+        else process_window<MODE>(C, w, buf, pos - j, u0);
+    }
+}
+
+// One consumer warp's share of a staged tile under a role filter.  Per round
+// a lane takes NCH chunks, c0 + lane + 32k (k < NCH; 16 sampled positions);
+// successive rounds of the CTA's warps step through the tile.  A chunk's
+// last positions need the next chunk's roles: from the next lane, from lane
+// 0's next chunk for lane 31, and for lane 31's last chunk (which belongs to
+// another warp) every second gram counts as present.  Windows start at
+// buffer positions [0, tile); chunk nchunks (the first chunk of the next
+// tile, in the halo) adds its position 0, which stands for this tile's last
+// windows.  Survivors are queued per warp (16-bit positions, appended with
+// one shared atomic per lane) and processed one per lane, in full rounds of
+// 32 and, after the last round, the rest.
+//   rfilt: the bit set in shared memory; rshift: DevTable::rf_shift;
+//   qcount: the warp's queue length in shared memory (0 on entry and exit).
+template <int STEP, int MODE, bool DEFER>
+__device__ __forceinline__ void consume_tile_rf(const WinCtx &C, const WarpCtx &w, uint16_t *q,
+                                                uint32_t *qcount, const uint8_t *buf, uint64_t u0,
+                                                uint32_t nchunks, uint32_t tile,
+                                                const uint8_t *rfilt, uint32_t rshift,
+                                                uint32_t warp, uint32_t nw, uint32_t lane,
+                                                const CandList *cc) {
+    constexpr uint32_t NCH = STEP == 2 ? 2 : 4;
+    constexpr uint32_t kFull = 0xffffffffu;
+    const uint32_t lastc = tile / 16u;  // the halo chunk: the highest chunk read
+    const uint32_t nch = nchunks + 1;   // chunks with sampled positions to test
+    const uint32_t step = nw * 32u * NCH;
+    const uint32_t src = (lane + 1u) & 31u;
+    uint32_t qn = 0;  // warp-uniform queue length
+    uint32_t c0 = warp * 32u * NCH;
+    uint4 v[NCH];
+#pragma unroll
+    for (uint32_t k = 0; k < NCH; ++k)
+        v[k] = *reinterpret_cast<const uint4 *>(buf + 16u * min(c0 + lane + 32u * k, lastc));
+    for (;;) {
+        const bool last = c0 >= nch;
+        if (!last) {
+            uint4 nv[NCH];
+#pragma unroll
+            for (uint32_t k = 0; k < NCH; ++k)
+                nv[k] = *reinterpret_cast<const uint4 *>(
+                    buf + 16u * min(c0 + step + lane + 32u * k, lastc));
+            // the next chunk's first word (step 2 only)
+            uint32_t v4[NCH];
+            if constexpr (STEP == 2) {
+#pragma unroll
+                for (uint32_t k = 0; k + 1 < NCH; ++k)
+                    v4[k] = __shfl_sync(kFull, lane == 0 ? v[k + 1].x : v[k].x, src);
+                uint32_t t = __shfl_sync(kFull, v[NCH - 1].x, src);
+                if (lane == 31)
+                    t = *reinterpret_cast<const uint32_t *>(buf +
+                                                            16u * min(c0 + 32u * NCH, lastc));
+                v4[NCH - 1] = t;
+            } else {
+#pragma unroll
+                for (uint32_t k = 0; k < NCH; ++k) v4[k] = 0;
+            }
+            uint32_t acc[NCH];
+#pragma unroll
+            for (uint32_t k = 0; k < NCH; ++k) acc[k] = rf_chunk<STEP>(v[k], v4[k], rfilt, rshift);
+            uint32_t m = 0;  // the round's candidates (see rf_pos)
+#pragma unroll
+            for (uint32_t k = 0; k < NCH; ++k) {
+                uint32_t an =
+                    __shfl_sync(kFull, (k + 1 < NCH && lane == 0) ? acc[k + 1] : acc[k], src);
+                if (k + 1 == NCH && lane == 31) an = 0xFFFFFFFFu;
+                const uint32_t c = c0 + lane + 32u * k;
+                const uint32_t mk = rf_cands<STEP>(acc[k], an);
+                m |= (c < nchunks ? mk : (c == nchunks ? mk & (1u << 28) : 0u)) << k;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < NCH; ++k) v[k] = nv[k];
+            const uint32_t cbase = c0 + lane;
+            c0 += step;
+            const uint32_t cnt = __popc(m);
+            const uint32_t total = __reduce_add_sync(kFull, cnt);
+            if (total == 0) continue;
+            if (qn + total <= kQueueCap) {
+                if (cnt) {
+                    uint32_t at = atomicAdd(qcount, cnt);
+                    while (m) {
+                        const uint32_t b = 31u - __clz(m);
+                        m &= ~(1u << b);
+                        q[at++] = (uint16_t)rf_pos<STEP>(cbase, b);
+                    }
+                }
+                qn += total;
+                __syncwarp();
+            } else {
+                // more survivors than the queue holds: each lane works through its own
+                while (m) {
+                    const uint32_t b = 31u - __clz(m);
+                    m &= ~(1u << b);
+                    rf_windows<STEP, MODE, DEFER>(C, w, cc, buf, rf_pos<STEP>(cbase, b), u0, tile);
+                }
+                if (DEFER) cand_flush(C, w, *cc, buf, u0, lane);
+                else flush(w, lane);
+            }
+        }
+        // full rounds of queued positions, one per lane; after the last round
+        // the rest
+        if (qn >= 32 || (last && qn)) {
+            while (qn >= 32 || (last && qn)) {
+                const uint32_t take = min(qn, 32u);
+                qn -= take;
+                if (lane < take) rf_windows<STEP, MODE, DEFER>(C, w, cc, buf, q[qn + lane], u0, tile);
+                __syncwarp();
+                if (DEFER) {
+                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kCandBuf - 32)
+                        cand_flush(C, w, *cc, buf, u0, lane);
+                } else if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32) {
+                    flush(w, lane);
+                }
+            }
+            if (lane == 0) *qcount = qn;
+            __syncwarp();
+        }
+        if (last) break;
+    }
+    if (DEFER) cand_flush(C, w, *cc, buf, u0, lane);
+    else flush(w, lane);
+}
+
 }  // namespace rk

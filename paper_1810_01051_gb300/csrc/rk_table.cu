@@ -137,13 +137,70 @@ bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_
     return true;
 }
 
+// Role filter of the patterns for sampling step `step` (see DevTable): the
+// grams at offsets j < step of every pattern with their roles, in a flat bit
+// set of 2^bits bits.  Role S sets two bits of the gram's word (at lo + 31
+// and lo + 28, the slot of a fourth role), and the scan asks for both, so a
+// text gram that is no key passes as S about as often as two set bits line
+// up, like L with B.  Step 4 needs every pattern to have at least 7 bytes.
+// Step 2 needs at least 5, or 4 bytes: a 4-byte pattern P has no gram at
+// offset 1, so for an occurrence at an odd x the gram at p = x + 1 holds
+// P[1..4) and one text byte; every such gram (256 of them) gets role S.
+// Returns false when the patterns do not allow the step or the set would be
+// too dense (more than one key per 16 bits at the largest size).
+constexpr uint32_t kRoleMaxLog2Bits = 19;   // 64 KiB of shared memory
+constexpr uint32_t kRoleMaxWild = 64;       // 4-byte patterns a step-2 filter takes
+constexpr uint32_t kRoleBitsPerKey = 16;    // least bits per key
+
+bool make_role_filter(const uint8_t *patterns, const std::vector<uint64_t> &src_off,
+                      const std::vector<uint32_t> &plen, uint32_t step,
+                      std::vector<uint32_t> *img, uint32_t *log2_bits) {
+    const uint32_t k = (uint32_t)plen.size();
+    uint32_t lmin = UINT32_MAX, n4 = 0;
+    for (uint32_t L : plen) {
+        lmin = std::min(lmin, L);
+        n4 += L == 4;
+    }
+    if (step == 4 ? lmin < 7 : (lmin < 4 || n4 > kRoleMaxWild)) return false;
+    std::vector<std::pair<uint32_t, uint32_t>> keys;  // (gram, role 0 S / 1 L / 2 B)
+    keys.reserve((size_t)k * step * 2 + (size_t)n4 * 256);
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint8_t *p = patterns + src_off[i];
+        const uint32_t L = plen[i];
+        for (uint32_t j = 0; j < step; ++j) {
+            if (j + 4 <= L) {
+                const bool longer = L >= j + 8;  // a second gram follows
+                keys.emplace_back(prefix_key(p + j, 4), longer ? 1u : 0u);
+                if (longer) keys.emplace_back(prefix_key(p + j + 4, 4), 2u);
+            } else {  // step 2, L = 4, j = 1: P[1..4) and any byte
+                const uint32_t g3 = prefix_key(p + 1, 3);
+                for (uint32_t c = 0; c < 256; ++c) keys.emplace_back(g3 | (c << 24), 0u);
+            }
+        }
+    }
+    const uint64_t nk = keys.size();
+    const uint32_t bits =
+        std::min<uint32_t>(kRoleMaxLog2Bits, std::max<uint32_t>(15, ceil_log2(nk * 512)));
+    if (nk * kRoleBitsPerKey > (1ull << bits)) return false;
+    const uint32_t wbits = bits - 5;
+    img->assign(1u << wbits, 0u);
+    for (const auto &kr : keys) {
+        const uint32_t lo = kr.first * kRoleMult;
+        uint32_t &word = (*img)[lo >> (32 - wbits)];
+        word |= 1u << ((lo + 31u - kr.second) & 31u);
+        if (kr.second == 0) word |= 1u << ((lo + 28u) & 31u);  // S's second bit
+    }
+    *log2_bits = bits;
+    return true;
+}
+
 }  // namespace
 
 // Serialise the pattern table of one pattern set into a host image; every
 // part is 256-byte aligned and the image ends on a 256-byte boundary.
 int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32_t base_log2,
                uint32_t filter_opt, uint32_t filter_bits_opt, uint32_t sample_opt,
-               TableBlob *out) {
+               uint32_t role_opt, TableBlob *out) {
     // ---- patterns ---------------------------------------------------------
     std::vector<uint64_t> src_off(k), poff(k);
     std::vector<uint32_t> plen(k);
@@ -208,8 +265,23 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     if (!make_filter(gram_keys, filter_opt, filter_bits_opt, false, &mode, &fbits, &fimg, &fmask))
         return RK_EINVAL;
 
+    // ---- role filter: sampled grams with their roles ------------------------
+    std::vector<uint32_t> rimg;
+    uint32_t rstep = 0, rbits = 0;
+    // chosen by the builder only when the prefilter is too (RK_FILTER_AUTO)
+    const bool role_ok = role_opt > 1 || (role_opt == 0 && filter_opt == RK_FILTER_AUTO);
+    if (role_ok && mode != kFilterNone && q == 4 && k > 0) {
+        for (uint32_t step : {4u, 2u}) {
+            if (role_opt > 1 && role_opt != step) continue;
+            if (make_role_filter(patterns, src_off, plen, step, &rimg, &rbits)) {
+                rstep = step;
+                break;
+            }
+        }
+    }
+
     // ---- sampled stage 1: 4-byte grams at offsets 0..3, their offset sets --
-    const bool sampled = sample_opt != 1 && mode != kFilterNone && q == 4 && lmin >= 7;
+    const bool sampled = !rstep && sample_opt != 1 && mode != kFilterNone && q == 4 && lmin >= 7;
     std::vector<SampSlot> smap;
     std::vector<uint32_t> simg;
     uint32_t smap_bits = 0, smode = 0, sbits = 0, smask_addr = 0;
@@ -287,6 +359,7 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     size_t o_lens = b.add(lengths.size() * 4 + 4);
     size_t o_smap = b.add(smap.size() * sizeof(SampSlot) + 8);
     size_t o_sfilter = b.add(simg.size() * 4 + 16);  // after the survivor tables: not staged with them
+    size_t o_rfilter = b.add(rimg.size() * 4 + 16);
     b.add(0);  // the blob ends on a 256-byte boundary: whole 16-byte copies stay inside
     uint8_t *hb = b.bytes.data();
     if (!fimg.empty()) memcpy(hb + o_filter, fimg.data(), fimg.size() * 4);
@@ -301,6 +374,7 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     if (!lengths.empty()) memcpy(hb + o_lens, lengths.data(), lengths.size() * 4);
     if (!smap.empty()) memcpy(hb + o_smap, smap.data(), smap.size() * sizeof(SampSlot));
     if (!simg.empty()) memcpy(hb + o_sfilter, simg.data(), simg.size() * 4);
+    if (!rimg.empty()) memcpy(hb + o_rfilter, rimg.data(), rimg.size() * 4);
 
     if (b.bytes.size() - o_grams > 0xFFFFFFFFull) return RK_EINVAL;  // tables above 4 GiB
     TableBlob &tb = *out;
@@ -316,6 +390,7 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     tb.o_lens = o_lens;
     tb.o_smap = o_smap;
     tb.o_sfilter = o_sfilter;
+    tb.o_rfilter = o_rfilter;
     DevTable &d = tb.meta;
     d = DevTable{};
     d.filter_bytes = (uint32_t)(fimg.size() * 4);
@@ -333,10 +408,14 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     d.sfilter_mode = smode;
     d.sfilter_mask = smask_addr;
     d.smap_bits = smap_bits;
+    d.rf_step = rstep;
+    d.rfilter_bytes = (uint32_t)(rimg.size() * 4);
+    d.rf_shift = rstep ? 30 - (rbits - 5) : 0;
     d.s2_bytes = (uint32_t)(o_sfilter - o_grams);
     tb.n_grams = D;
     tb.filter_log2_bits = mode == kFilterNone ? 0 : fbits;
     tb.sfilter_log2_bits = sampled ? sbits : 0;
+    tb.rfilter_log2_bits = rstep ? rbits : 0;
     tb.bytes = std::move(b.bytes);
     return RK_OK;
 }
@@ -356,6 +435,7 @@ void bind_blob(DevTable *d, const TableBlob &b, const uint8_t *dm) {
     d->lengths = (const uint32_t *)(dm + b.o_lens);
     d->smap = (const SampSlot *)(dm + b.o_smap);
     d->sfilter = (const uint32_t *)(dm + b.o_sfilter);
+    d->rfilter = (const uint32_t *)(dm + b.o_rfilter);
     d->s2_base = dm + b.o_grams;
 }
 
@@ -366,7 +446,7 @@ namespace {
 
 // rk_build_opts with the defaults filled in.
 struct Opts {
-    uint32_t base_log2, filter, filter_log2_bits, warps, tile, stages, cps, sample;
+    uint32_t base_log2, filter, filter_log2_bits, warps, tile, stages, cps, sample, role;
 };
 
 // Check the patterns' count and lengths and the options (no CUDA call).
@@ -388,6 +468,7 @@ int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
     r.stages = o.stages ? o.stages : 2;
     r.cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
     r.sample = o.sample;
+    r.role = o.role_step;
     if (r.base_log2 < 1 || r.base_log2 > 60) return RK_EINVAL;
     if (r.filter > RK_FILTER_NONE) return RK_EINVAL;
     // survivor positions within a tile are 16-bit
@@ -395,6 +476,7 @@ int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
         r.stages < 2 || r.stages > 8 || r.cps < 1 || r.cps > 8)
         return RK_EINVAL;
     if (r.sample > 1) return RK_EINVAL;
+    if (r.role != 0 && r.role != 1 && r.role != 2 && r.role != 4) return RK_EINVAL;
     *out = r;
     return RK_OK;
 }
@@ -410,11 +492,14 @@ int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const 
     if (smem_optin / cps <= 1024) return RK_EINVAL;
 
     int rc = build_blob(patterns, lens, k, o.base_log2, o.filter, o.filter_log2_bits, o.sample,
-                        tb);
+                        o.role, tb);
     if (rc) return rc;
     const uint32_t lmax = tb->meta.lmax;
-    // either bit set (prefixes, or the sampled grams) is staged at offset 0
-    const uint32_t fbytes = std::max(tb->meta.filter_bytes, tb->meta.sfilter_bytes);
+    // the bit set a scan stages at offset 0: the role filter when there is
+    // one, else the prefixes' or (deferred scans) the sampled grams'
+    const uint32_t fbytes = tb->meta.rf_step
+                                ? tb->meta.rfilter_bytes
+                                : std::max(tb->meta.filter_bytes, tb->meta.sfilter_bytes);
     const uint64_t s2_total = tb->meta.s2_bytes;
 
     // ---- launch shape: shrink stages / tile until shared memory fits -------
@@ -445,7 +530,8 @@ int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const 
 }
 
 rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
-                        uint32_t filter_log2_bits, uint32_t sfilter_log2_bits, uint32_t sm_count,
+                        uint32_t filter_log2_bits, uint32_t sfilter_log2_bits,
+                        uint32_t rfilter_log2_bits, uint32_t sm_count,
                         uint32_t device, uint64_t device_bytes) {
     rk_table_info r{};
     r.n_patterns = d.n_patterns;
@@ -472,6 +558,8 @@ rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
     r.device_bytes = device_bytes;
     r.sample_step = d.sample;
     r.sample_filter_log2_bits = sfilter_log2_bits;
+    r.role_step = d.rf_step;
+    r.role_filter_log2_bits = rfilter_log2_bits;
     return r;
 }
 
@@ -521,6 +609,7 @@ extern "C" int rk_build(const uint8_t *patterns, const uint32_t *lens, uint32_t 
     t->n_grams = tb.n_grams;
     t->filter_log2_bits = tb.filter_log2_bits;
     t->sfilter_log2_bits = tb.sfilter_log2_bits;
+    t->rfilter_log2_bits = tb.rfilter_log2_bits;
     t->filter_opt = o.filter;
     *out = t;
     return RK_OK;
@@ -536,7 +625,8 @@ extern "C" int rk_plan(const uint8_t *patterns, const uint32_t *lens, uint32_t k
     Tuning tune{};
     rc = plan_table(patterns, lens, k, o, smem_optin, &tb, &tune);
     if (rc) return rc;
-    *info = make_info(tb.meta, tune, tb.n_grams, tb.filter_log2_bits, tb.sfilter_log2_bits, 0,
+    *info = make_info(tb.meta, tune, tb.n_grams, tb.filter_log2_bits, tb.sfilter_log2_bits,
+                      tb.rfilter_log2_bits, 0,
                       UINT32_MAX, tb.bytes.size());
     return RK_OK;
 }
@@ -563,6 +653,7 @@ extern "C" void rk_destroy(rk_table *t) {
 extern "C" int rk_table_info_get(const rk_table *t, rk_table_info *info) {
     if (!t || !info) return RK_EINVAL;
     *info = make_info(t->dev, t->tune, t->n_grams, t->filter_log2_bits, t->sfilter_log2_bits,
+                      t->rfilter_log2_bits,
                       (uint32_t)t->sm_count, (uint32_t)t->device, t->d_bytes);
     return RK_OK;
 }

@@ -48,7 +48,7 @@ class RkError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "base_log2", "filter", "filter_log2_bits", "warps", "tile_bytes", "stages", "ctas_per_sm",
-        "sample")]
+        "sample", "role_step")]
 
 
 class TableInfo(ctypes.Structure):
@@ -57,7 +57,8 @@ class TableInfo(ctypes.Structure):
         "filter_log2_bits", "filter_smem_bytes", "n_grams", "warps", "tile_bytes", "stages",
         "ctas_per_sm", "halo_bytes", "smem_bytes", "sm_count", "device", "s2_smem_bytes")] + [
         ("device_bytes", ctypes.c_uint64)] + [
-        (n, ctypes.c_uint32) for n in ("sample_step", "sample_filter_log2_bits")]
+        (n, ctypes.c_uint32) for n in ("sample_step", "sample_filter_log2_bits", "role_step",
+                                       "role_filter_log2_bits")]
 
 
 class BatchOpts(ctypes.Structure):
@@ -239,13 +240,13 @@ def _stream(stream) -> int:
 
 def rk_build(patterns: Sequence[bytes], base_log2: int = 0, filter: int = RK_FILTER_AUTO,
              filter_log2_bits: int = 0, warps: int = 0, tile_bytes: int = 0, stages: int = 0,
-             ctas_per_sm: int = 0, sample: int = 0) -> int:
+             ctas_per_sm: int = 0, sample: int = 0, role_step: int = 0) -> int:
     """Build a table from a sequence of byte strings; returns the handle."""
     L = load()
     lens = np.array([len(p) for p in patterns], dtype=np.uint32)
     cat = np.frombuffer(b"".join(bytes(p) for p in patterns) or b"\0", dtype=np.uint8).copy()
     opts = BuildOpts(base_log2, filter, filter_log2_bits, warps, tile_bytes, stages, ctas_per_sm,
-                     sample)
+                     sample, role_step)
     out = ctypes.c_void_p()
     _check(L.rk_build(cat.ctypes.data if len(patterns) else None,
                       lens.ctypes.data if len(patterns) else None,
@@ -259,7 +260,8 @@ GB300_SMEM_OPTIN = 232448
 
 def rk_plan(patterns: Sequence[bytes], smem_optin: int = GB300_SMEM_OPTIN, base_log2: int = 0,
             filter: int = RK_FILTER_AUTO, filter_log2_bits: int = 0, warps: int = 0,
-            tile_bytes: int = 0, stages: int = 0, ctas_per_sm: int = 0, sample: int = 0) -> dict:
+            tile_bytes: int = 0, stages: int = 0, ctas_per_sm: int = 0, sample: int = 0,
+            role_step: int = 0) -> dict:
     """What rk_build would give these patterns on a device with `smem_optin`
     bytes of opt-in shared memory per block, worked out on the host (no GPU);
     the keys of rk_table_info."""
@@ -267,7 +269,7 @@ def rk_plan(patterns: Sequence[bytes], smem_optin: int = GB300_SMEM_OPTIN, base_
     lens = np.array([len(p) for p in patterns], dtype=np.uint32)
     cat = np.frombuffer(b"".join(bytes(p) for p in patterns) or b"\0", dtype=np.uint8).copy()
     opts = BuildOpts(base_log2, filter, filter_log2_bits, warps, tile_bytes, stages, ctas_per_sm,
-                     sample)
+                     sample, role_step)
     info = TableInfo()
     _check(L.rk_plan(cat.ctypes.data if len(patterns) else None,
                      lens.ctypes.data if len(patterns) else None,

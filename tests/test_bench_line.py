@@ -113,8 +113,11 @@ def test_bench_line(monkeypatch, capsys, cpu_baseline):
     assert roof["achieved"] == pytest.approx((small.n + 8 * expect_m) / 0.5e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
     prof = bench.read_profile()
-    assert roof["traffic"] == prof["dram_bytes_per_full_launch"]
-    assert roof["integer_pipes"]["alu_pipe_frac"] == prof["tile_scan_alu_pipe_frac"]
+    if prof is None:  # figures taken on other sources are not reported
+        assert roof["traffic"] is None and roof["integer_pipes"] is None
+    else:
+        assert roof["traffic"] == prof["dram_bytes_per_full_launch"]
+        assert roof["integer_pipes"]["alu_pipe_frac"] == prof["tile_scan_alu_pipe_frac"]
     e2e = line["e2e"]
     assert e2e["h2d_bytes_per_step"] == small.n and e2e["d2h_bytes_per_step"] == 16 + 8 * expect_m
     if cpu_baseline:

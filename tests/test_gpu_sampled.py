@@ -1,9 +1,11 @@
 """GPU parity of the sampled deferred scan (every pattern at least 7 bytes:
 stage 1 tests every 4th position against the patterns' 4-byte grams at
-offsets 0..3) against the oracle, bit-exact, with the edge cases of the
-sampling: windows ending at tile boundaries (found through the next tile's
-first word), grams repeated at several offsets, the shortest allowed
-patterns, and texts ending at every offset of a 16-byte chunk."""
+offsets 0..3; tables built without a role filter, role_step = 1) against the
+oracle, bit-exact, with the edge cases of the sampling: windows ending at
+tile boundaries (found through the next tile's first word), grams repeated
+at several offsets, the shortest allowed patterns, and texts ending at every
+offset of a 16-byte chunk.  The edge cases also run with the builder's
+choice, which for these small sets is the role filter with step 4."""
 
 import numpy as np
 import pytest
@@ -50,7 +52,7 @@ def test_fuzz_sampled(seed):
     lmin = int(rng.integers(7, 12))
     lmax = lmin + int(rng.integers(0, 60))
     w = random_small(seed + 900, n, k, lmin, lmax, alphabet=alpha, plants=4)
-    opts = OPTS[seed % len(OPTS)]
+    opts = dict(OPTS[seed % len(OPTS)], role_step=1)
     assert sample_step(w.patterns, **opts) == 4
     expect = oracle.rabin_karp(w.text, w.patterns)
     mis = int(rng.integers(0, 16))
@@ -66,9 +68,10 @@ def test_repeated_grams_and_shortest_patterns():
                          dtype=np.uint8)
     pats = [b"abababa", b"bababab", b"aaaaaaa", b"aaaaaaaa", b"abcabca", b"cabcabcabca",
             b"ababababab", b"aaaaaaaaaaab", b"xyzxyzx"]
-    assert sample_step(pats) == 4
+    assert sample_step(pats, role_step=1) == 4
     expect = oracle.bruteforce(text, pats)
-    for opts in (dict(), dict(tile_bytes=1024, stages=2, warps=2)):
+    for opts in (dict(role_step=1), dict(tile_bytes=1024, stages=2, warps=2, role_step=1),
+                 dict(), dict(tile_bytes=1024, stages=2, warps=2)):
         for mis in (0, 1, 2, 3, 9):
             assert_same(deferred_search(pats, text, mis, **opts), expect, f"{opts} mis {mis}")
 
@@ -83,7 +86,8 @@ def test_text_end_offsets(tail):
     pats = [bytes(text[n - L:].tolist()) for L in (7, 8, 11, 19)]
     pats += [bytes(text[s:s + 9].tolist()) for s in (0, 1, 2, 3)]
     expect = oracle.bruteforce(text, pats)
-    for opts in (dict(), dict(tile_bytes=2048, stages=2, warps=2)):
+    for opts in (dict(role_step=1), dict(tile_bytes=2048, stages=2, warps=2, role_step=1),
+                 dict(), dict(tile_bytes=2048, stages=2, warps=2)):
         for mis in (0, 5, 12):
             assert_same(deferred_search(pats, text, mis, **opts), expect,
                         f"tail {tail} {opts} mis {mis}")
@@ -101,9 +105,9 @@ def test_sampling_off_same_list():
 
 
 def test_short_pattern_disables_sampling():
-    assert sample_step([b"abcdefg", b"abcdef"]) == 1
-    assert sample_step([b"abcdefg", b"abcdefgh"]) == 4
-    assert sample_step([b"abcdefg"], filter=rk.RK_FILTER_NONE) == 1
+    assert sample_step([b"abcdefg", b"abcdef"], role_step=1) == 1
+    assert sample_step([b"abcdefg", b"abcdefgh"], role_step=1) == 4
+    assert sample_step([b"abcdefg"], filter=rk.RK_FILTER_NONE, role_step=1) == 1
 
 
 def test_list_overflow_sampled():
@@ -114,8 +118,10 @@ def test_list_overflow_sampled():
     text = np.full(n, ord("a"), dtype=np.uint8)
     text[::1009] = ord("b")
     pats = [b"aaaaaaa", b"aaaaaaaa", b"aaaaaaaaaaa", b"aaaaaaaaaaaab", b"baaaaaa"]
-    assert sample_step(pats) == 4
+    assert sample_step(pats, role_step=1) == 4
     expect = oracle.bruteforce(text, pats)
     assert expect[0].size > n // 64 + 4096
     for mis in (0, 3):
-        assert_same(deferred_search(pats, text, mis), expect, f"overflow mis {mis}")
+        for opts in (dict(role_step=1), dict()):
+            assert_same(deferred_search(pats, text, mis, **opts), expect,
+                        f"overflow mis {mis} {opts}")

@@ -80,20 +80,96 @@ def test_filter_layout_and_size(name):
     assert rep["filter_smem_bytes"] == (1 << 11) // 8 * 32
 
 
+def role_keys(patterns, step):
+    """Role-filter keys for sampling step `step` counted in Python: per
+    pattern, the gram at each offset j < step (and the one 4 bytes on when the
+    pattern has j + 8 bytes), or for a 4-byte pattern at j = 1 the 256 grams
+    P[1..4) + any byte; None when the step does not apply."""
+    lens = [len(p) for p in patterns]
+    if step == 4 and min(lens) < 7:
+        return None
+    if step == 2 and (min(lens) < 4 or sum(L == 4 for L in lens) > 64):
+        return None
+    n = 0
+    for L in lens:
+        for j in range(step):
+            if j + 4 <= L:
+                n += 2 if L >= j + 8 else 1
+            else:
+                n += 256
+    return n
+
+
+def role_rule(patterns, role_step=0, filter=rk.RK_FILTER_AUTO):
+    """(step, log2 bits) of the role filter the builder should choose: its
+    own choice only with the prefilter's (RK_FILTER_AUTO)."""
+    if min(len(p) for p in patterns) < 4 or filter == rk.RK_FILTER_NONE:
+        return 0, 0
+    if role_step == 0 and filter != rk.RK_FILTER_AUTO:
+        return 0, 0
+    for step in (4, 2):
+        if role_step not in (0, step):
+            continue
+        nk = role_keys(patterns, step)
+        if nk is None:
+            continue
+        bits = min(19, max(15, ceil_log2(nk * 512)))
+        if nk * 16 <= 1 << bits:
+            return step, bits
+    return 0, 0
+
+
 @pytest.mark.parametrize("name", ["zipf", "signature", "dna", "short", "long"])
 def test_sampling_rule(name):
     pats = pattern_sets()[name]
     info = rk.rk_plan(pats)
-    if min(len(p) for p in pats) >= 7:
-        # every window holds one position = 0 mod 4 within its first 7 bytes
-        assert info["sample_step"] == 4
-        G = sampled_grams(pats)
-        want = 14 if G <= 256 else min(19, max(15, ceil_log2(32 * G)))
-        assert info["sample_filter_log2_bits"] == want
-        off = rk.rk_plan(pats, sample=1)
-        assert off["sample_step"] == 1 and off["sample_filter_log2_bits"] == 0
-    else:
-        assert info["sample_step"] == 1 and info["sample_filter_log2_bits"] == 0
+    step, bits = role_rule(pats)
+    assert (info["role_step"], info["role_filter_log2_bits"]) == (step, bits)
+    none = rk.rk_plan(pats, role_step=1)
+    assert none["role_step"] == 0 and none["role_filter_log2_bits"] == 0
+    for forced in (2, 4):
+        want = role_rule(pats, forced)
+        got = rk.rk_plan(pats, role_step=forced)
+        assert (got["role_step"], got["role_filter_log2_bits"]) == want
+    for filt in (rk.RK_FILTER_FLAT, rk.RK_FILTER_REPLICATED):
+        assert rk.rk_plan(pats, filter=filt)["role_step"] == 0
+        got = rk.rk_plan(pats, filter=filt, role_step=4)
+        assert (got["role_step"], got["role_filter_log2_bits"]) == role_rule(pats, 4, filt)
+    for opts, has_role in ((dict(), step != 0), (dict(role_step=1), False)):
+        info = rk.rk_plan(pats, **opts)
+        if min(len(p) for p in pats) >= 7 and not has_role:
+            # every window holds one position = 0 mod 4 within its first 7 bytes
+            assert info["sample_step"] == 4
+            G = sampled_grams(pats)
+            want = 14 if G <= 256 else min(19, max(15, ceil_log2(32 * G)))
+            assert info["sample_filter_log2_bits"] == want
+            off = rk.rk_plan(pats, sample=1, **opts)
+            assert off["sample_step"] == 1 and off["sample_filter_log2_bits"] == 0
+        else:
+            # a role filter replaces the sampled grams' structures
+            assert info["sample_step"] == 1 and info["sample_filter_log2_bits"] == 0
+
+
+def test_role_filter_choice():
+    """The workloads' sets take the filter the rule predicts: a Zipf set (a
+    few 4-byte patterns) step 2 at 2^19 bits, the DNA set step 4, 2,000
+    signature patterns (about 16,000 role keys) step 4, the full 10,000 (about
+    79,000) none; patterns below 4 bytes, RK_FILTER_NONE, or more than 64
+    four-byte patterns rule it out."""
+    sets = pattern_sets()
+    z = rk.rk_plan(sets["zipf"])
+    assert (z["role_step"], z["role_filter_log2_bits"]) == (2, 19)
+    assert rk.rk_plan(sets["dna"])["role_step"] == 4
+    assert rk.rk_plan(sets["signature"])["role_step"] == 4
+    big = make_config(2, n=1 << 16, k=10000).patterns
+    assert rk.rk_plan(big)["role_step"] == 0
+    assert rk.rk_plan(sets["short"])["role_step"] == 0
+    assert rk.rk_plan(sets["zipf"], filter=rk.RK_FILTER_NONE)["role_step"] == 0
+    many4 = [bytes([65 + i % 26, 66 + i // 26, 67, 68]) for i in range(65)]
+    assert rk.rk_plan(many4)["role_step"] == 0
+    assert rk.rk_plan(many4[:64])["role_step"] == 2
+    with pytest.raises(rk.RkError):
+        rk.rk_plan(sets["zipf"], role_step=3)
 
 
 def test_shared_memory_fits_every_request():
@@ -167,7 +243,7 @@ def test_empty_set_and_rejections(lib):
     info = rk.rk_plan([])
     assert info["n_patterns"] == 0 and info["sample_step"] == 1
     for bad in (dict(base_log2=61), dict(filter=9), dict(tile_bytes=1000), dict(stages=1),
-                dict(warps=40), dict(sample=2), dict(ctas_per_sm=9)):
+                dict(warps=40), dict(sample=2), dict(role_step=3), dict(ctas_per_sm=9)):
         with pytest.raises(rk.RkError) as e:
             rk.rk_plan([b"ab"], **bad)
         assert e.value.code == rk.RK_EINVAL, bad
