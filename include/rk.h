@@ -77,10 +77,13 @@ typedef struct rk_build_opts {
                                   1 is the paper's shift-add base 2 */
     uint32_t filter;           /* RK_FILTER_* */
     uint32_t filter_log2_bits; /* prefilter size in bits, log2 (default: by pattern count) */
-    uint32_t warps;            /* consumer warps per CTA, 1..31 (default 24) */
+    uint32_t warps;            /* consumer warps per CTA, 1..31 (default 24; with a role
+                                  filter: stage-1 warps, default 16, plus up to 4 survivor
+                                  warps within 31) */
     uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16, <= 65536
-                                  (default 49152) */
-    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */
+                                  (default 49152; with a role filter 32768) */
+    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2; with a role
+                                  filter 3) */
     uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
     uint32_t sample;           /* 0: when every pattern has >= 7 bytes and no role filter is
                                   built, scans with a candidate list (rk_scan_device_ws) test
@@ -119,6 +122,8 @@ typedef struct rk_table_info {
     uint32_t role_step;        /* 2 or 4: the scans use a role filter (rk_build_opts.role_step);
                                   0: none */
     uint32_t role_filter_log2_bits;    /* its bit set's size (0 without) */
+    uint32_t survivor_warps;   /* role filter: warps per CTA that handle the windows stage 1
+                                  passes (warps counts the stage-1 warps); 0 without */
 } rk_table_info;
 
 /* Human-readable text of a status code (static storage). */

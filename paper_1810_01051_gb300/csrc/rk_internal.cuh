@@ -124,6 +124,7 @@ struct Tuning {
     uint32_t halo;         // bytes staged after each tile (multiple of 16, >= 16)
     uint32_t s2_smem;      // survivor-stage table bytes copied to shared memory (0: global)
     uint32_t smem_bytes;   // dynamic shared memory per CTA
+    uint32_t sv_warps;     // role-filter scans: survivor warps per CTA (0: other scans)
 };
 
 }  // namespace rk

@@ -81,7 +81,8 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     // they fit the shared memory sized for the table's tile.
     const uint64_t span = p.mis + x_end - p.u_first;
     const uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
-    const uint64_t round_bytes = (uint64_t)tu.warps * 1024u;
+    // (a stage-1 round of a warp: 1 KiB, or 2 KiB with a step-4 role filter)
+    const uint64_t round_bytes = (uint64_t)tu.warps * (t->dev.rf_step == 4 ? 2048u : 1024u);
     const uint64_t per_cta = (span + max_ctas - 1) / max_ctas;
     const uint32_t tile = (uint32_t)std::min<uint64_t>(
         tu.tile_bytes, std::max<uint64_t>(round_bytes, (per_cta + round_bytes - 1) / round_bytes *
@@ -104,9 +105,12 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     const uint32_t sm = tu.smem_bytes;
     cudaError_t e;
     if (t->dev.rf_step) {
-        // every scan of a table with a role filter stages that bit set
+        // every scan of a table with a role filter runs its own kernel, with
+        // that bit set staged and survivor warps beside the stage-1 warps
         p.tab.filter = t->dev.rfilter;
         p.tab.filter_bytes = t->dev.rfilter_bytes;
+        p.sv_warps = tu.sv_warps;
+        threads = (tu.warps + tu.sv_warps + 1) * 32;
         e = scan::launch_role(p, grid, threads, sm, stream, t->dev.rf_step);
         return e == cudaSuccess ? RK_OK : RK_ECUDA;
     }

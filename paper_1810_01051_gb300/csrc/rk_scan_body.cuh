@@ -255,14 +255,10 @@ __device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w
 constexpr uint32_t kCandSlotShift = 40;          // text offsets are below 2^40
 constexpr uint32_t kCandBuf = kMatchCap / 2;     // 16-byte candidates in a warp's match buffer
 
-// The prefix-map slot whose lengths apply to the window at pos (exact
-// prefix; a length below q + 4, or the next four bytes in the slot's
-// fingerprint set), or -1; *v8: the window's bytes 0..7, little-endian.
-template <class Src, class Pos>
-__device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos pos,
-                                           uint64_t *v8) {
-    const uint64_t v = ld8(src, pos);  // window bytes 0..7, little-endian
-    *v8 = v;
+// The prefix-map slot whose lengths apply to a window whose bytes 0..7 are v
+// (little-endian): exact prefix, and a length below q + 4 or the next four
+// bytes in the slot's fingerprint set; -1 if none.
+__device__ __forceinline__ int gram_lookup_v8(const WinCtx &C, uint64_t v) {
     const uint32_t key = C.q == 4 ? (uint32_t)v : (uint32_t)v & ((1u << (8u * C.q)) - 1u);
     const uint32_t gmask = (1u << C.gram_bits) - 1u;
     uint32_t idx = (key * kGramMult) >> (32u - C.gram_bits);
@@ -275,6 +271,14 @@ __device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos 
         }
         idx = (idx + 1) & gmask;
     }
+}
+
+template <class Src, class Pos>
+__device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos pos,
+                                           uint64_t *v8) {
+    const uint64_t v = ld8(src, pos);  // window bytes 0..7, little-endian
+    *v8 = v;
+    return gram_lookup_v8(C, v);
 }
 
 // Probe every length of prefix-map slot gi that applies to the window at pos
@@ -657,140 +661,57 @@ __device__ __forceinline__ uint32_t rf_pos(uint32_t cbase, uint32_t b) {
     return 16u * (cbase + 32u * (b & 3u)) + (uint32_t)STEP * (7u - (b >> 2));
 }
 
-// The windows a sampled position pos stands for: pos - j, j < STEP, those
-// that start in this tile ([0, tile); windows before it belong to the
-// previous tile).  DEFER: stage 2a, candidates to the list; else stage 2.
-template <int STEP, int MODE, bool DEFER>
-__device__ __forceinline__ void rf_windows(const WinCtx &C, const WarpCtx &w, const CandList *cc,
-                                           const uint8_t *buf, uint32_t pos, uint64_t u0,
-                                           uint32_t tile) {
-#pragma unroll 1
-    for (uint32_t j = 0; j < (uint32_t)STEP; ++j) {
-        if (pos < j || pos - j >= tile) continue;
-        if (DEFER) cand_window(C, w, *cc, buf, pos - j, u0);
-        else process_window<MODE>(C, w, buf, pos - j, u0);
+// A window (buffer position ua, bytes 0..7 in v8) of a role-filter
+// survivor: stage 2a (DEFER: the candidate to the warp's buffer, or to the
+// list when that is full, or probed at once when the list is full too) or
+// stage 2 (the rest of a longer window read from the text in global memory).
+template <bool DEFER>
+__device__ __forceinline__ void rf_window_g(const WinCtx &C, const WarpCtx &w, const CandList *cc,
+                                            const GText &g, uint64_t ua, uint64_t v8) {
+    if (ua < C.lo || ua >= C.hi) return;
+    const int gi = gram_lookup_v8(C, v8);
+    if (gi < 0) return;
+    const uint64_t x = ua - C.mis;
+    const WText win{g, ua, v8};
+    if (!DEFER) {
+        probe_slot(C, w, win, ua, x, (uint32_t)gi);
+        return;
     }
+    const ulonglong2 c = make_ulonglong2(x | ((uint64_t)gi << kCandSlotShift), v8);
+    const uint32_t s = atomicAdd(w.mcount, 1u);
+    if (s < kCandBuf) {
+        reinterpret_cast<ulonglong2 *>(w.mbuf)[s] = c;
+        return;
+    }
+    const unsigned long long k = atomicAdd(cc->count, 1ull);
+    if (k < cc->cap) cc->list[k] = c;
+    else probe_slot<true>(C, w, win, ua, x, (uint32_t)gi);
 }
 
-// One consumer warp's share of a staged tile under a role filter.  Per round
-// a lane takes NCH chunks, c0 + lane + 32k (k < NCH; 16 sampled positions);
-// successive rounds of the CTA's warps step through the tile.  A chunk's
-// last positions need the next chunk's roles: from the next lane, from lane
-// 0's next chunk for lane 31, and for lane 31's last chunk (which belongs to
-// another warp) every second gram counts as present.  Windows start at
-// buffer positions [0, tile); chunk nchunks (the first chunk of the next
-// tile, in the halo) adds its position 0, which stands for this tile's last
-// windows.  Survivors are queued per warp (16-bit positions, appended with
-// one shared atomic per lane) and processed one per lane, in full rounds of
-// 32 and, after the last round, the rest.
-//   rfilt: the bit set in shared memory; rshift: DevTable::rf_shift;
-//   qcount: the warp's queue length in shared memory (0 on entry and exit).
-template <int STEP, int MODE, bool DEFER>
-__device__ __forceinline__ void consume_tile_rf(const WinCtx &C, const WarpCtx &w, uint16_t *q,
-                                                uint32_t *qcount, const uint8_t *buf, uint64_t u0,
-                                                uint32_t nchunks, uint32_t tile,
-                                                const uint8_t *rfilt, uint32_t rshift,
-                                                uint32_t warp, uint32_t nw, uint32_t lane,
-                                                const CandList *cc) {
-    constexpr uint32_t NCH = STEP == 2 ? 2 : 4;
-    constexpr uint32_t kFull = 0xffffffffu;
-    const uint32_t lastc = tile / 16u;  // the halo chunk: the highest chunk read
-    const uint32_t nch = nchunks + 1;   // chunks with sampled positions to test
-    const uint32_t step = nw * 32u * NCH;
-    const uint32_t src = (lane + 1u) & 31u;
-    uint32_t qn = 0;  // warp-uniform queue length
-    uint32_t c0 = warp * 32u * NCH;
-    uint4 v[NCH];
-#pragma unroll
-    for (uint32_t k = 0; k < NCH; ++k)
-        v[k] = *reinterpret_cast<const uint4 *>(buf + 16u * min(c0 + lane + 32u * k, lastc));
-    for (;;) {
-        const bool last = c0 >= nch;
-        if (!last) {
-            uint4 nv[NCH];
-#pragma unroll
-            for (uint32_t k = 0; k < NCH; ++k)
-                nv[k] = *reinterpret_cast<const uint4 *>(
-                    buf + 16u * min(c0 + step + lane + 32u * k, lastc));
-            // the next chunk's first word (step 2 only)
-            uint32_t v4[NCH];
-            if constexpr (STEP == 2) {
-#pragma unroll
-                for (uint32_t k = 0; k + 1 < NCH; ++k)
-                    v4[k] = __shfl_sync(kFull, lane == 0 ? v[k + 1].x : v[k].x, src);
-                uint32_t t = __shfl_sync(kFull, v[NCH - 1].x, src);
-                if (lane == 31)
-                    t = *reinterpret_cast<const uint32_t *>(buf +
-                                                            16u * min(c0 + 32u * NCH, lastc));
-                v4[NCH - 1] = t;
+// Warp-converged: the warp's buffered candidates to the list with one
+// atomic; those beyond its capacity are probed here from global memory.
+__device__ __forceinline__ void rf_cand_flush(const WinCtx &C, const WarpCtx &w,
+                                              const CandList &cc, const GText &g, uint32_t lane) {
+    __syncwarp();
+    const uint32_t cnt = min(*reinterpret_cast<volatile uint32_t *>(w.mcount), kCandBuf);
+    if (cnt) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cc.count, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const ulonglong2 *cb = reinterpret_cast<const ulonglong2 *>(w.mbuf);
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            const ulonglong2 c = cb[i];
+            if (base + i < cc.cap) {
+                cc.list[base + i] = c;
             } else {
-#pragma unroll
-                for (uint32_t k = 0; k < NCH; ++k) v4[k] = 0;
-            }
-            uint32_t acc[NCH];
-#pragma unroll
-            for (uint32_t k = 0; k < NCH; ++k) acc[k] = rf_chunk<STEP>(v[k], v4[k], rfilt, rshift);
-            uint32_t m = 0;  // the round's candidates (see rf_pos)
-#pragma unroll
-            for (uint32_t k = 0; k < NCH; ++k) {
-                uint32_t an =
-                    __shfl_sync(kFull, (k + 1 < NCH && lane == 0) ? acc[k + 1] : acc[k], src);
-                if (k + 1 == NCH && lane == 31) an = 0xFFFFFFFFu;
-                const uint32_t c = c0 + lane + 32u * k;
-                const uint32_t mk = rf_cands<STEP>(acc[k], an);
-                m |= (c < nchunks ? mk : (c == nchunks ? mk & (1u << 28) : 0u)) << k;
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < NCH; ++k) v[k] = nv[k];
-            const uint32_t cbase = c0 + lane;
-            c0 += step;
-            const uint32_t cnt = __popc(m);
-            const uint32_t total = __reduce_add_sync(kFull, cnt);
-            if (total == 0) continue;
-            if (qn + total <= kQueueCap) {
-                if (cnt) {
-                    uint32_t at = atomicAdd(qcount, cnt);
-                    while (m) {
-                        const uint32_t b = 31u - __clz(m);
-                        m &= ~(1u << b);
-                        q[at++] = (uint16_t)rf_pos<STEP>(cbase, b);
-                    }
-                }
-                qn += total;
-                __syncwarp();
-            } else {
-                // more survivors than the queue holds: each lane works through its own
-                while (m) {
-                    const uint32_t b = 31u - __clz(m);
-                    m &= ~(1u << b);
-                    rf_windows<STEP, MODE, DEFER>(C, w, cc, buf, rf_pos<STEP>(cbase, b), u0, tile);
-                }
-                if (DEFER) cand_flush(C, w, *cc, buf, u0, lane);
-                else flush(w, lane);
+                const uint64_t x = c.x & ((1ull << kCandSlotShift) - 1ull);
+                probe_slot<true>(C, w, g, x + C.mis, x, (uint32_t)(c.x >> kCandSlotShift));
             }
         }
-        // full rounds of queued positions, one per lane; after the last round
-        // the rest
-        if (qn >= 32 || (last && qn)) {
-            while (qn >= 32 || (last && qn)) {
-                const uint32_t take = min(qn, 32u);
-                qn -= take;
-                if (lane < take) rf_windows<STEP, MODE, DEFER>(C, w, cc, buf, q[qn + lane], u0, tile);
-                __syncwarp();
-                if (DEFER) {
-                    if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kCandBuf - 32)
-                        cand_flush(C, w, *cc, buf, u0, lane);
-                } else if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32) {
-                    flush(w, lane);
-                }
-            }
-            if (lane == 0) *qcount = qn;
-            __syncwarp();
-        }
-        if (last) break;
     }
-    if (DEFER) cand_flush(C, w, *cc, buf, u0, lane);
-    else flush(w, lane);
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile uint32_t *>(w.mcount) = 0;
+    __syncwarp();
 }
 
 }  // namespace rk

@@ -1,7 +1,6 @@
-// Scan kernel variants with a role filter: stage 1 looks up every 2nd or
-// 4th position's 4-byte gram (DevTable::rf_step), in scans that verify
-// their survivors themselves or list them for the verification kernel.
-#include "rk_scan_kernel.cuh"
+// The role-filter scan kernel's variants: sampling step 2 or 4, survivors
+// verified in the scan or listed for the verification kernel.
+#include "rk_scan_rf.cuh"
 
 namespace rk {
 namespace scan {
@@ -10,10 +9,10 @@ cudaError_t launch_role(const ScanParams &p, uint32_t grid, uint32_t threads, ui
                         cudaStream_t st, uint32_t step) {
     const bool defer = p.cand.list != nullptr;
     if (step == 2)
-        return defer ? launch_d<kFilterFlat, true, true, 2>(p, grid, threads, smem, st)
-                     : launch_d<kFilterFlat, true, false, 2>(p, grid, threads, smem, st);
-    return defer ? launch_d<kFilterFlat, true, true, 4>(p, grid, threads, smem, st)
-                 : launch_d<kFilterFlat, true, false, 4>(p, grid, threads, smem, st);
+        return defer ? launch_rf_d<2, true>(p, grid, threads, smem, st)
+                     : launch_rf_d<2, false>(p, grid, threads, smem, st);
+    return defer ? launch_rf_d<4, true>(p, grid, threads, smem, st)
+                 : launch_rf_d<4, false>(p, grid, threads, smem, st);
 }
 
 }  // namespace scan

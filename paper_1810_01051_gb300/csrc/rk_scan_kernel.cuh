@@ -22,6 +22,7 @@ struct ScanParams {
     unsigned long long *info;
     uint64_t timeout_ns;     // limit of every pipeline wait
     uint32_t tile, stages, halo, warps, s2_smem;
+    uint32_t sv_warps;       // role-filter kernel: survivor warps
     uint32_t withhold;       // diagnostics: the producer issues no copy at all
     CandList cand;           // deferred verification: candidate list (DEFER kernels)
 };
@@ -34,8 +35,8 @@ struct ScanParams {
 // rk_verify_kernel).
 // SAMP: 0, every position against the prefix bit set; 1 (DEFER, q = 4),
 // every 4th position against the bit set of the patterns' grams at offsets
-// 0..3; 2 or 4 (MODE flat, q = 4), every 2nd or 4th position against the
-// role filter (P.tab.filter is the bit set staged in each case).
+// 0..3 (P.tab.filter is the bit set staged in each case).  Tables with a
+// role filter have a kernel of their own (rk_scan_rf.cuh).
 template <int MODE, bool Q4, int MAXW, bool S2S, bool DEFER, int SAMP>
 __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_tiles_kernel(const __grid_constant__ ScanParams P) {
@@ -49,7 +50,6 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     uint64_t *empty = full + P.stages;
     uint16_t *queues = reinterpret_cast<uint16_t *>(smem + lay.queue_off);
     uint32_t *mcount = reinterpret_cast<uint32_t *>(smem + lay.mcount_off);
-    uint32_t *qcount = reinterpret_cast<uint32_t *>(smem + lay.qcount_off);
     uint64_t *mbuf = reinterpret_cast<uint64_t *>(smem + lay.match_off);
     uint8_t *stage0 = smem + lay.stage_off;
 
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         s_abort = 0;
         fence_mbar_init();
     }
-    if (tid < nw) mcount[tid] = qcount[tid] = 0;
+    if (tid < nw) mcount[tid] = 0;
     __syncthreads();
 
     const uint64_t my_tiles =
@@ -140,10 +140,7 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
         const uint64_t u0 = P.u_first + t * P.tile;
         const uint64_t wend = min(u0 + P.tile, C.hi);
         const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
-        if constexpr (SAMP >= 2)
-            consume_tile_rf<SAMP, MODE, DEFER>(C, w, q, qcount + warp, buf, u0, nchunks, P.tile,
-                                               sfilt, P.tab.rf_shift, warp, nw, lane, &P.cand);
-        else if constexpr (SAMP == 1)
+        if constexpr (SAMP == 1)
             consume_tile_s4<MODE>(C, w, q, buf, u0, nchunks, P.tile, sfilt, fmask, lane4, warp, nw,
                                   lane, P.cand);
         else
@@ -179,9 +176,7 @@ cudaError_t launch_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint3
 template <int MODE, bool Q4, bool DEFER, int SAMP>
 cudaError_t launch_d(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                      cudaStream_t st) {
-    // (the role-filter variants take the 16-warp register budget for fewer warps)
-    if constexpr (SAMP < 2)
-        if (p.warps <= 8) return launch_w<MODE, Q4, 8, DEFER, SAMP>(p, grid, threads, smem, st);
+    if (p.warps <= 8) return launch_w<MODE, Q4, 8, DEFER, SAMP>(p, grid, threads, smem, st);
     if (p.warps <= 16) return launch_w<MODE, Q4, 16, DEFER, SAMP>(p, grid, threads, smem, st);
     if (p.warps <= 24) return launch_w<MODE, Q4, 24, DEFER, SAMP>(p, grid, threads, smem, st);
     return launch_w<MODE, Q4, 31, DEFER, SAMP>(p, grid, threads, smem, st);
@@ -202,7 +197,7 @@ inline cudaError_t launch_one(const ScanParams &p, uint32_t grid, uint32_t threa
 
 // Launchers of the variants, one translation unit each: the prefix bit set
 // without a filter, replicated or flat (SAMP 0, or SAMP 1 for deferred scans
-// of flat or replicated sets), and the role filter (MODE flat, q = 4).
+// of flat or replicated sets), and the role-filter kernel (rk_scan_rf.cuh).
 cudaError_t launch_none(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                         cudaStream_t st, bool q4);
 cudaError_t launch_replicated(const ScanParams &p, uint32_t grid, uint32_t threads,

@@ -151,6 +151,7 @@ bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_
 constexpr uint32_t kRoleMaxLog2Bits = 19;   // 64 KiB of shared memory
 constexpr uint32_t kRoleMaxWild = 64;       // 4-byte patterns a step-2 filter takes
 constexpr uint32_t kRoleBitsPerKey = 16;    // least bits per key
+constexpr uint32_t kRfSurvivorWarps = 4;    // survivor warps of the role-filter scan kernel
 
 bool make_role_filter(const uint8_t *patterns, const std::vector<uint64_t> &src_off,
                       const std::vector<uint32_t> &plen, uint32_t step,
@@ -462,18 +463,19 @@ int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
     r.base_log2 = o.base_log2 ? o.base_log2 : 8;
     r.filter = o.filter;
     r.filter_log2_bits = o.filter_log2_bits;
-    r.warps = o.warps ? o.warps : 24;
-    // default: 48 KiB tiles (two 24 KiB rounds of 24 warps), two in flight
-    r.tile = o.tile_bytes ? o.tile_bytes : 49152;
-    r.stages = o.stages ? o.stages : 2;
+    // warps, tile and stages stay 0 (default) here: plan_table picks them
+    // by the kind of stage-1 filter the table gets
+    r.warps = o.warps;
+    r.tile = o.tile_bytes;
+    r.stages = o.stages;
     r.cps = o.ctas_per_sm ? o.ctas_per_sm : 1;
     r.sample = o.sample;
     r.role = o.role_step;
     if (r.base_log2 < 1 || r.base_log2 > 60) return RK_EINVAL;
     if (r.filter > RK_FILTER_NONE) return RK_EINVAL;
     // survivor positions within a tile are 16-bit
-    if (r.warps < 1 || r.warps > 31 || r.tile < 1024 || r.tile % 16 || r.tile > kMaxTileBytes ||
-        r.stages < 2 || r.stages > 8 || r.cps < 1 || r.cps > 8)
+    if (r.warps > 31 || (r.tile && (r.tile < 1024 || r.tile % 16 || r.tile > kMaxTileBytes)) ||
+        (r.stages && (r.stages < 2 || r.stages > 8)) || r.cps < 1 || r.cps > 8)
         return RK_EINVAL;
     if (r.sample > 1) return RK_EINVAL;
     if (r.role != 0 && r.role != 1 && r.role != 2 && r.role != 4) return RK_EINVAL;
@@ -486,14 +488,26 @@ int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
 // block.  No CUDA call.
 int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const Opts &o,
                uint32_t smem_optin, TableBlob *tb, Tuning *tune) {
-    uint32_t tile = o.tile, stages = o.stages;
-    const uint32_t warps = o.warps, cps = o.cps;
+    const uint32_t cps = o.cps;
     // room for the static shared memory of each CTA
     if (smem_optin / cps <= 1024) return RK_EINVAL;
 
     int rc = build_blob(patterns, lens, k, o.base_log2, o.filter, o.filter_log2_bits, o.sample,
                         o.role, tb);
     if (rc) return rc;
+    const bool role = tb->meta.rf_step != 0;
+    // Defaults.  Prefix filter: 24 warps, 48 KiB tiles (two 24 KiB rounds of
+    // 24 warps), two in flight.  Role filter: 16 stage-1 warps, 32 KiB tiles
+    // (two 16 KiB rounds), three in flight, and kRfSurvivorWarps survivor
+    // warps (fewer when the stage-1 warps leave less room under 31).
+    uint32_t warps = o.warps ? o.warps : (role ? 16u : 24u);
+    uint32_t tile = o.tile ? o.tile : (role ? 32768u : 49152u);
+    uint32_t stages = o.stages ? o.stages : (role ? 3u : 2u);
+    uint32_t sv = 0;
+    if (role) {
+        sv = std::min<uint32_t>(kRfSurvivorWarps, std::max<uint32_t>(1, 31 - warps));
+        warps = std::min<uint32_t>(warps, 31 - sv);
+    }
     const uint32_t lmax = tb->meta.lmax;
     // the bit set a scan stages at offset 0: the role filter when there is
     // one, else the prefixes' or (deferred scans) the sampled grams'
@@ -508,24 +522,29 @@ int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const 
     // The survivor-stage tables go to shared memory when they fit beside the
     // requested pipeline (or beside a two-stage one); otherwise they are read
     // from global memory (L2).
+    // the shared memory of either scan kernel
+    auto total = [&](uint32_t s2b, uint32_t st, uint32_t tl) {
+        return role ? rf_smem_layout(fbytes, s2b, sv, st, tl, halo).total
+                    : smem_layout(fbytes, s2b, warps, st, tl, halo).total;
+    };
     uint32_t s2 = 0;
     if (s2_total <= limit) {
-        if (smem_layout(fbytes, (uint32_t)s2_total, warps, stages, tile, halo).total <= limit) {
+        if (total((uint32_t)s2_total, stages, tile) <= limit) {
             s2 = (uint32_t)s2_total;
-        } else if (smem_layout(fbytes, (uint32_t)s2_total, warps, 2, tile, halo).total <= limit) {
+        } else if (total((uint32_t)s2_total, 2, tile) <= limit) {
             s2 = (uint32_t)s2_total;
             stages = 2;
         }
     }
-    SmemLayout lay = smem_layout(fbytes, s2, warps, stages, tile, halo);
-    while (lay.total > limit) {
+    uint32_t bytes = total(s2, stages, tile);
+    while (bytes > limit) {
         if (stages > 2) --stages;
         else if (tile > 4 * halo && tile > 4096) tile /= 2;
         else return RK_EINVAL;
         tile = tile / 16 * 16;
-        lay = smem_layout(fbytes, s2, warps, stages, tile, halo);
+        bytes = total(s2, stages, tile);
     }
-    *tune = Tuning{warps, tile, stages, cps, halo, s2, lay.total};
+    *tune = Tuning{warps, tile, stages, cps, halo, s2, bytes, sv};
     return RK_OK;
 }
 
@@ -560,6 +579,7 @@ rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
     r.sample_filter_log2_bits = sfilter_log2_bits;
     r.role_step = d.rf_step;
     r.role_filter_log2_bits = rfilter_log2_bits;
+    r.survivor_warps = tune.sv_warps;
     return r;
 }
 

@@ -52,7 +52,13 @@ def test_pattern_statistics(name):
     info = rk.rk_plan(pats)
     for key, val in stats(pats).items():
         assert info[key] == val, key
-    assert info["base_log2"] == 8 and info["warps"] == 24
+    assert info["base_log2"] == 8
+    if info["role_step"]:
+        # role filter: 16 stage-1 warps, 4 survivor warps, 32 KiB tiles, three stages
+        assert (info["warps"], info["survivor_warps"]) == (16, 4)
+        assert info["tile_bytes"] <= 32768 and info["stages"] <= 3
+    else:
+        assert info["warps"] == 24 and info["survivor_warps"] == 0
     assert info["sm_count"] == 0 and info["device"] == 0xFFFFFFFF
 
 
@@ -191,7 +197,14 @@ def test_shared_memory_fits_every_request():
         assert info["tile_bytes"] % 16 == 0 and info["tile_bytes"] >= 1024
         assert 2 <= info["stages"] <= opts["stages"]
         assert info["tile_bytes"] <= opts["tile_bytes"]
-        assert info["warps"] == opts["warps"] and info["ctas_per_sm"] == opts["ctas_per_sm"]
+        if info["role_step"]:
+            # stage-1 warps plus 1..4 survivor warps within 31
+            sv = min(4, max(1, 31 - opts["warps"]))
+            assert info["survivor_warps"] == sv
+            assert info["warps"] == min(opts["warps"], 31 - sv)
+        else:
+            assert info["warps"] == opts["warps"] and info["survivor_warps"] == 0
+        assert info["ctas_per_sm"] == opts["ctas_per_sm"]
         # asking for the chosen pipeline gives it again; only the survivor
         # tables may now move to shared memory (their place is decided
         # before the tile shrinks)
@@ -204,17 +217,18 @@ def test_shared_memory_fits_every_request():
             assert again == info
 
 
-def test_stages_then_tiles_shrink():
+@pytest.mark.parametrize("role_step,optin", [(1, 166912), (0, 120000)])
+def test_stages_then_tiles_shrink(role_step, optin):
     pats = pattern_sets()["zipf"]
-    full = rk.rk_plan(pats, stages=2)
+    full = rk.rk_plan(pats, stages=2, role_step=role_step)
     # more stages than fit: stages drop first, the tile stays
-    many = rk.rk_plan(pats, stages=8)
+    many = rk.rk_plan(pats, stages=8, role_step=role_step)
     assert many["tile_bytes"] == full["tile_bytes"] and many["stages"] < 8
     # a device with less shared memory: the tile halves until it fits
-    small = rk.rk_plan(pats, smem_optin=166912)
+    small = rk.rk_plan(pats, smem_optin=optin, role_step=role_step)
     assert small["stages"] == 2 and small["tile_bytes"] < full["tile_bytes"]
     assert full["tile_bytes"] % small["tile_bytes"] == 0
-    assert small["smem_bytes"] <= 166912 - 1024
+    assert small["smem_bytes"] <= optin - 1024
 
 
 def test_survivor_tables_in_shared_memory_only_when_they_fit():
