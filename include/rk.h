@@ -237,7 +237,9 @@ int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
                      uint64_t capacity, uint64_t *d_info, void *d_workspace,
                      uint64_t workspace_bytes, void *stream);
 
-/* Host-buffer search: copies h_text to the device in chunks (overlapping the
+/* Host-buffer search (Section 1's problem on a host text; the whole of
+ * Section 3.1's GPU path: the text copied to the device, the kernel, the
+ * result copied back): copies h_text to the device in chunks (overlapping the
  * copies with the scan), sorts, and copies the sorted keys back.  Blocks until
  * done.  *n_matches receives the match count; if it exceeds capacity the call
  * returns RK_ECAPACITY and h_keys is left untouched.  Device buffers are cached
@@ -245,6 +247,46 @@ int rk_search_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
  * Errors: RK_EINVAL, RK_ENOMEM, RK_ECAPACITY, RK_ECUDA, RK_ETIMEOUT.         */
 int rk_search(const rk_table *t, const uint8_t *h_text, uint64_t n, uint64_t *h_keys,
               uint64_t capacity, uint64_t *n_matches);
+
+/* ---- match records ---------------------------------------------------------
+ * The result of Section 1's problem as records instead of packed keys, and a
+ * table built from one pointer per pattern: thin calls over rk_build,
+ * rk_search and rk_search_device.  The record list is in ascending
+ * (pattern_id, offset) order, like the keys.                                */
+typedef struct rk_match {
+    uint64_t offset;      /* the match starts at text byte `offset` */
+    uint32_t pattern_id;  /* index of the pattern in the set */
+    uint32_t reserved;    /* 0 */
+} rk_match;
+
+/* rk_build with the patterns given as n_patterns pointers (patterns[i] points
+ * to lens[i] bytes; the bytes are copied).  Errors as rk_build (a null
+ * pattern pointer: RK_EINVAL).                                              */
+int rk_build_ptrs(const uint8_t *const *patterns, const uint32_t *lens, uint32_t n_patterns,
+                  const rk_build_opts *opts, rk_table **out);
+
+/* Host-buffer search returning a record list the library allocates: on
+ * RK_OK, *out holds *n_out records (free it with rk_free_matches; it is a
+ * valid pointer even when *n_out is 0).  Blocks until done.  Runs
+ * rk_search, twice when its first guess at the count was short.  On error
+ * *out is NULL and *n_out 0.  Errors: as rk_search (RK_ECAPACITY only for
+ * 2^32 or more matches).                                                    */
+int rk_search_matches(const rk_table *t, const uint8_t *h_text, uint64_t n, rk_match **out,
+                      uint64_t *n_out);
+
+/* Device-buffer search into records: rk_search_device on `stream` with the
+ * table's cached workspace, the sorted keys turned into records in
+ * d_out[0..capacity) (device memory, 8-byte aligned), then the count copied
+ * back: the call waits for `stream`.  *n_out (host memory) receives the
+ * match count; if it exceeds capacity the call returns RK_ECAPACITY and
+ * d_out holds no valid list (call again with *n_out records of room).  Calls
+ * on one table are serialised (the cached workspace).
+ * Errors: RK_EINVAL, RK_ENOMEM, RK_ECAPACITY, RK_ECUDA, RK_ETIMEOUT.         */
+int rk_search_device_matches(const rk_table *t, const uint8_t *d_text, uint64_t n, void *stream,
+                             rk_match *d_out, uint64_t capacity, uint64_t *n_out);
+
+/* Free a record list from rk_search_matches (NULL is ignored).              */
+void rk_free_matches(rk_match *m);
 
 /* Rabin hash of every length-L window (Section 3.1's hash h = h*B + c,
  * reduced mod 2^61-1, B = 2^base_log2), by a tiled rolling update:
@@ -265,6 +307,11 @@ int rk_window_hashes_device(const uint8_t *d_text, uint64_t n, uint32_t L, uint3
  * Errors: RK_EINVAL, RK_ECUDA.                                               */
 int rk_paper_search_device(const uint8_t *d_text, uint64_t n, const uint8_t *h_pattern, uint32_t m,
                            uint8_t *d_result, uint32_t threads_per_block, void *stream);
+
+/* The GPU architecture the library's kernels were built for, as
+ * cudaFuncGetAttributes reports it on the current device (major * 10 +
+ * minor: 103 for sm_103a).  Errors: RK_EINVAL (null), RK_ECUDA.             */
+int rk_debug_binary_version(int *version);
 
 /* Diagnostics for failure detection: rk_scan_device with the producer
  * issuing no copy, so every pipeline wait runs out after timeout_ms
@@ -438,18 +485,22 @@ int rk_server_stats_get(rk_server *s, rk_server_stats *stats);
  * or latency-bound loops that cannot afford cudaMalloc/cudaFree, which may
  * synchronise the device.  rk_search_device_noalloc does what
  * rk_search_device does, but the sort's scratch space is a fixed array inside
- * the library (RK_NOALLOC_MAX_KEYS keys: about 12 MB), reserved on every GPU
- * where the library's device code is loaded and held until the process exits.
- * It allocates nothing.
+ * the library (RK_NOALLOC_MAX_KEYS keys: RK_NOALLOC_SCRATCH_BYTES bytes, about
+ * 16.8 MB), reserved on every GPU where the library's device code is loaded
+ * and held until the process exits.  It allocates nothing.
  *   - capacity > RK_NOALLOC_MAX_KEYS is rejected with RK_EINVAL;
  *   - the first call on each device looks up the array's device address
- *     (once per device, with that device current): make that first call
- *     before any stream capture;
+ *     (once per device, with that device current) and keeps it: make that
+ *     first call before any stream capture; a device reset (cudaDeviceReset,
+ *     or anything else that destroys the device's primary context) unloads
+ *     the array, and the kept address must not be used after it, so do not
+ *     call this entry point in a process after resetting a device it ran on;
  *   - every call on a device shares the one array, and it keeps the last
  *     call's contents: calls that overlap on the GPU (other streams, other
  *     threads, other tables) race on it and must be serialised by the caller.
  * Other arguments, results and errors as rk_search_device.                  */
 #define RK_NOALLOC_MAX_KEYS (1u << 20)
+#define RK_NOALLOC_SCRATCH_BYTES 16785920u
 int rk_search_device_noalloc(const rk_table *t, const uint8_t *d_text, uint64_t n,
                              uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
                              void *stream);

@@ -1,6 +1,9 @@
 // Public entry points of rk.h: device-buffer scan / sort / search, the
 // host-buffer search with copy/scan overlap, and the per-window hash kernel.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "rk_internal.cuh"
 #include "rk_sortws.cuh"
@@ -293,4 +296,140 @@ extern "C" int rk_debug_scan_withheld(const rk_table *t, const uint8_t *d_text, 
     if (cudaMemsetAsync(d_info, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return RK_ECUDA;
     return launch_scan_opts(t, d_text, n, 0, n, d_keys, capacity, d_info, st,
                             (uint64_t)timeout_ms * 1000000ull, true);
+}
+
+// ---------------------------------------------------------------- match records
+
+namespace {
+
+// Sorted keys -> match records, for the first min(count, capacity) keys
+// (count read on the device).
+__global__ void rk_keys_to_matches_kernel(const uint64_t *keys, const uint64_t *info,
+                                          uint64_t capacity, rk_match *out) {
+    const uint64_t m = min((uint64_t)info[0], capacity);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        out[i] = rk_match{RK_KEY_OFFSET(k), RK_KEY_ID(k), 0u};
+    }
+}
+
+}  // namespace
+
+extern "C" int rk_build_ptrs(const uint8_t *const *patterns, const uint32_t *lens,
+                             uint32_t n_patterns, const rk_build_opts *opts, rk_table **out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    if (n_patterns > RK_MAX_PATTERNS) return RK_EINVAL;
+    if (n_patterns && (!patterns || !lens)) return RK_EINVAL;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < n_patterns; ++i) {
+        if (lens[i] < 1 || lens[i] > RK_MAX_PATTERN_LEN || !patterns[i]) return RK_EINVAL;
+        total += lens[i];
+    }
+    std::vector<uint8_t> cat;
+    try {
+        cat.resize(total ? total : 1);
+    } catch (...) {
+        return RK_ENOMEM;
+    }
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < n_patterns; ++i) {
+        memcpy(cat.data() + at, patterns[i], lens[i]);
+        at += lens[i];
+    }
+    return rk_build(n_patterns ? cat.data() : nullptr, n_patterns ? lens : nullptr, n_patterns,
+                    opts, out);
+}
+
+extern "C" void rk_free_matches(rk_match *m) { free(m); }
+
+extern "C" int rk_search_matches(const rk_table *t, const uint8_t *h_text, uint64_t n,
+                                 rk_match **out, uint64_t *n_out) {
+    if (!out || !n_out) return RK_EINVAL;
+    *out = nullptr;
+    *n_out = 0;
+    if (!t || n > RK_MAX_TEXT_LEN || (n && !h_text)) return RK_EINVAL;
+    // a first guess at the count; a second search runs when it was short
+    uint64_t cap = std::min<uint64_t>(n / 256 + 4096, 1ull << 22);
+    std::vector<uint64_t> keys;
+    for (;;) {
+        try {
+            keys.resize(cap);
+        } catch (...) {
+            return RK_ENOMEM;
+        }
+        uint64_t m = 0;
+        const int rc = rk_search(t, h_text, n, keys.data(), cap, &m);
+        if (rc == RK_ECAPACITY && m > cap) {
+            if (m >= (1ull << 32)) return RK_ECAPACITY;  // beyond rk_search's output limit
+            cap = m;
+            continue;
+        }
+        if (rc) return rc;
+        rk_match *r = static_cast<rk_match *>(malloc(std::max<uint64_t>(m, 1) * sizeof(rk_match)));
+        if (!r) return RK_ENOMEM;
+        for (uint64_t i = 0; i < m; ++i)
+            r[i] = rk_match{RK_KEY_OFFSET(keys[i]), RK_KEY_ID(keys[i]), 0u};
+        *out = r;
+        *n_out = m;
+        return RK_OK;
+    }
+}
+
+extern "C" int rk_search_device_matches(const rk_table *tc, const uint8_t *d_text, uint64_t n,
+                                        void *stream, rk_match *d_out, uint64_t capacity,
+                                        uint64_t *n_out) {
+    if (!n_out) return RK_EINVAL;
+    *n_out = 0;
+    if (!tc || n > RK_MAX_TEXT_LEN || (n && !d_text) || (capacity && !d_out) ||
+        !aligned(d_out, 8) || capacity >= (1ull << 32))
+        return RK_EINVAL;
+    int rc = check_device(tc);
+    if (rc) return rc;
+    rk_table *t = const_cast<rk_table *>(tc);  // only the host-path cache is mutated
+    std::lock_guard<std::mutex> lock(t->host_mu);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // key buffer, header and workspace (the sort's, then the candidate list)
+    // cached on the table like rk_search's
+    const uint64_t kcap = std::max<uint64_t>(capacity, 2);
+    uint64_t cap_bytes = t->h_keys_cap;
+    if ((rc = ensure(reinterpret_cast<void **>(&t->h_keys), &cap_bytes, kcap * 8))) return rc;
+    t->h_keys_cap = cap_bytes;
+    uint64_t info_cap = t->h_info ? 16 : 0;
+    if ((rc = ensure(reinterpret_cast<void **>(&t->h_info), &info_cap, 16))) return rc;
+    const uint64_t sort_bytes = sort_workspace_bytes(kcap);
+    const uint64_t scan_bytes = can_defer(t) ? scan_ws_layout(n).total : 0;
+    if ((rc = ensure(&t->h_ws, &t->h_ws_cap, sort_bytes + scan_bytes))) return rc;
+    rc = rk_search_device(t, d_text, n, t->h_keys, capacity, t->h_info, t->h_ws,
+                          sort_bytes + scan_bytes, stream);
+    if (rc) return rc;
+    if (capacity) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return RK_ECUDA;
+        const uint64_t blocks = std::min<uint64_t>((capacity + 255) / 256, (uint64_t)sms * 4);
+        rk_keys_to_matches_kernel<<<(uint32_t)blocks, 256, 0, st>>>(t->h_keys, t->h_info,
+                                                                  capacity, d_out);
+        if (cudaGetLastError() != cudaSuccess) return RK_ECUDA;
+    }
+    uint64_t info[2] = {0, 0};
+    if (cudaMemcpyAsync(info, t->h_info, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RK_ECUDA;
+    *n_out = info[0];
+    if (info[1] != RK_OK) return (int)info[1];
+    return info[0] > capacity ? RK_ECAPACITY : RK_OK;
+}
+
+extern "C" int rk_debug_binary_version(int *version) {
+    if (!version) return RK_EINVAL;
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, rk_keys_to_matches_kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return RK_ECUDA;
+    }
+    *version = a.binaryVersion;
+    return RK_OK;
 }

@@ -21,6 +21,7 @@ namespace {
 // workspace for that capacity (ping-pong key buffer, digit totals and
 // look-back words).
 constexpr uint64_t kNoAllocBytes = rk::sort_ws_bytes(RK_NOALLOC_MAX_KEYS);
+static_assert(kNoAllocBytes == RK_NOALLOC_SCRATCH_BYTES, "rk.h states the scratch size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -30,7 +31,9 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
 // per device.  In host code the array's name is only a stand-in, so the
-// address must come from the runtime.
+// address must come from the runtime.  The address kept here dies with the
+// device's primary context (a device reset unloads the array); rk.h tells
+// callers not to use this entry point after resetting a device.
 int scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return RK_EINVAL;
     std::lock_guard<std::mutex> lock(g_setup_mu);

@@ -24,6 +24,7 @@ RK_MAX_TEXT_LEN = (1 << 40) - 1
 RK_KEY_OFFSET_BITS = 40
 RK_FILTER_AUTO, RK_FILTER_REPLICATED, RK_FILTER_FLAT, RK_FILTER_NONE = range(4)
 RK_NOALLOC_MAX_KEYS = 1 << 20
+RK_NOALLOC_SCRATCH_BYTES = 16785920
 
 #: names of every function include/rk.h declares
 EXPORTS = [
@@ -35,7 +36,8 @@ EXPORTS = [
     "rk_batch_info_get", "rk_batch_set", "rk_batch_run", "rk_batch_results", "rk_batch_read",
     "rk_batch_autotune", "rk_server_create", "rk_server_destroy", "rk_server_submit",
     "rk_server_take", "rk_server_stats_get", "rk_paper_search_device",
-    "rk_debug_scan_withheld",
+    "rk_debug_scan_withheld", "rk_build_ptrs", "rk_search_matches", "rk_search_device_matches",
+    "rk_free_matches", "rk_debug_binary_version",
 ]
 
 
@@ -49,6 +51,16 @@ class BuildOpts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "base_log2", "filter", "filter_log2_bits", "warps", "tile_bytes", "stages", "ctas_per_sm",
         "sample", "role_step")]
+
+
+class Match(ctypes.Structure):
+    """rk_match: one (pattern id, offset) record."""
+    _fields_ = [("offset", ctypes.c_uint64), ("pattern_id", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+#: numpy view of an rk_match array
+MATCH_DTYPE = np.dtype([("offset", np.uint64), ("pattern_id", np.uint32), ("reserved", np.uint32)])
 
 
 class TableInfo(ctypes.Structure):
@@ -175,6 +187,16 @@ def load() -> ctypes.CDLL:
     L.rk_paper_search_device.argtypes = [vp, u64, vp, u32, vp, u32, vp]
     L.rk_debug_scan_withheld.restype = ctypes.c_int
     L.rk_debug_scan_withheld.argtypes = [vp, vp, u64, vp, u64, vp, u32, vp]
+    L.rk_build_ptrs.restype = ctypes.c_int
+    L.rk_build_ptrs.argtypes = [vp, vp, u32, ctypes.POINTER(BuildOpts), ctypes.POINTER(vp)]
+    L.rk_search_matches.restype = ctypes.c_int
+    L.rk_search_matches.argtypes = [vp, vp, u64, ctypes.POINTER(vp), ctypes.POINTER(u64)]
+    L.rk_search_device_matches.restype = ctypes.c_int
+    L.rk_search_device_matches.argtypes = [vp, vp, u64, vp, vp, u64, ctypes.POINTER(u64)]
+    L.rk_free_matches.restype = None
+    L.rk_free_matches.argtypes = [vp]
+    L.rk_debug_binary_version.restype = ctypes.c_int
+    L.rk_debug_binary_version.argtypes = [ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -361,6 +383,57 @@ def rk_search(table: int, h_text, n: int, h_keys, capacity: int) -> Tuple[int, i
     if rc not in (RK_OK, RK_ECAPACITY):
         raise RkError(rc, "rk_search")
     return rc, int(cnt.value)
+
+
+def rk_build_ptrs(patterns: Sequence[bytes], **opts) -> int:
+    """rk_build from one pointer per pattern (the bytes stay in Python
+    buffers for the call); returns the handle."""
+    L = load()
+    bufs = [ctypes.create_string_buffer(bytes(p), max(len(p), 1)) for p in patterns]
+    ptrs = (ctypes.c_void_p * max(len(bufs), 1))(*[ctypes.addressof(b) for b in bufs])
+    lens = np.array([len(p) for p in patterns] or [0], dtype=np.uint32)
+    o = BuildOpts(*(opts.get(name, 0) for name, _ in BuildOpts._fields_))
+    out = ctypes.c_void_p()
+    _check(L.rk_build_ptrs(ctypes.addressof(ptrs) if patterns else None,
+                           lens.ctypes.data if patterns else None, len(patterns),
+                           ctypes.byref(o), ctypes.byref(out)), "rk_build_ptrs")
+    return int(out.value)
+
+
+def rk_search_matches(table: int, h_text, n: int) -> np.ndarray:
+    """Host-buffer search into library-allocated records; returns a copy as a
+    numpy array of MATCH_DTYPE (the library's list is freed)."""
+    L = load()
+    out = ctypes.c_void_p()
+    cnt = ctypes.c_uint64(0)
+    _check(L.rk_search_matches(table, _buf(h_text, n, "h_text", False), n, ctypes.byref(out),
+                               ctypes.byref(cnt)), "rk_search_matches")
+    try:
+        m = int(cnt.value)
+        raw = ctypes.string_at(out.value, m * MATCH_DTYPE.itemsize) if m else b""
+        return np.frombuffer(raw, dtype=MATCH_DTYPE).copy()
+    finally:
+        L.rk_free_matches(out)
+
+
+def rk_search_device_matches(table: int, d_text, n: int, d_out, capacity: int,
+                             stream=None) -> Tuple[int, int]:
+    """Device-buffer search into records d_out[0..capacity).  Returns (status,
+    n_matches); RK_ECAPACITY is returned, not raised."""
+    cnt = ctypes.c_uint64(0)
+    rc = load().rk_search_device_matches(table, _buf(d_text, n, "d_text", True), n,
+                                         _stream(stream),
+                                         _buf(d_out, MATCH_DTYPE.itemsize * capacity, "d_out", True),
+                                         capacity, ctypes.byref(cnt))
+    if rc not in (RK_OK, RK_ECAPACITY):
+        raise RkError(rc, "rk_search_device_matches")
+    return rc, int(cnt.value)
+
+
+def rk_debug_binary_version() -> int:
+    v = ctypes.c_int(0)
+    _check(load().rk_debug_binary_version(ctypes.byref(v)), "rk_debug_binary_version")
+    return int(v.value)
 
 
 def rk_window_hashes_device(d_text, n: int, L: int, base_log2: int, d_hashes,

@@ -39,10 +39,10 @@ def test_every_declared_symbol_exported(lib):
         assert getattr(lib, name) is not None
 
 
-def test_library_is_for_sm103a(lib):
-    # the fatbinary names its target; cuobjdump only lists the architectures
-    out = subprocess.run(["cuobjdump", "--list-elf", build_lib.LIB], capture_output=True, text=True)
-    assert "sm_103a" in out.stdout, out.stdout + out.stderr
+def test_library_is_built_for_sm103a():
+    # every translation unit is compiled for sm_103a alone (a GPU test reads
+    # the kernels' binary version back through rk_debug_binary_version)
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def test_strerror(lib):
@@ -119,6 +119,21 @@ def test_handle_entry_points_reject_null(lib):
     assert lib.rk_server_take(None, 1, 0, None, 0, ctypes.byref(n), None) == rk.RK_EINVAL
     assert lib.rk_server_stats_get(None, None) == rk.RK_EINVAL
     assert lib.rk_search_device_noalloc(None, None, 0, None, 0, None, None) == rk.RK_EINVAL
+    cnt = ctypes.c_uint64(5)
+    mp = ctypes.c_void_p(7)
+    assert lib.rk_search_matches(None, None, 0, ctypes.byref(mp), ctypes.byref(cnt)) == rk.RK_EINVAL
+    assert mp.value is None and cnt.value == 0  # cleared on error
+    assert lib.rk_search_device_matches(None, None, 0, None, None, 0, ctypes.byref(cnt)) == rk.RK_EINVAL
+    assert lib.rk_debug_binary_version(None) == rk.RK_EINVAL
+    lib.rk_free_matches(None)
+    # a null pattern pointer or a bad length is refused before any CUDA call
+    a = ctypes.create_string_buffer(b"abc")
+    ptrs = (ctypes.c_void_p * 2)(ctypes.addressof(a), None)
+    lens = (ctypes.c_uint32 * 2)(3, 3)
+    assert lib.rk_build_ptrs(ptrs, lens, 2, None, ctypes.byref(mp)) == rk.RK_EINVAL
+    lens[1] = 0
+    ptrs[1] = ctypes.addressof(a)
+    assert lib.rk_build_ptrs(ptrs, lens, 2, None, ctypes.byref(mp)) == rk.RK_EINVAL
     # the paper's kernel checks its pattern and launch shape first
     pat = np.frombuffer(b"ACGT", dtype=np.uint8).copy()
     assert lib.rk_paper_search_device(None, 10, None, 4, None, 0, None) == rk.RK_EINVAL
@@ -152,7 +167,7 @@ def test_binding_types_match_header(lib):
 
 
 # ctypes mirror of each C struct: (C name, binding class)
-STRUCTS = [("rk_build_opts", "BuildOpts"), ("rk_table_info", "TableInfo"),
+STRUCTS = [("rk_build_opts", "BuildOpts"), ("rk_table_info", "TableInfo"), ("rk_match", "Match"),
            ("rk_batch_opts", "BatchOpts"), ("rk_batch_info", "BatchInfo"),
            ("rk_server_opts", "ServerOpts"), ("rk_request_times", "RequestTimes"),
            ("rk_server_stats", "ServerStats")]
