@@ -78,12 +78,11 @@ typedef struct rk_build_opts {
     uint32_t filter;           /* RK_FILTER_* */
     uint32_t filter_log2_bits; /* prefilter size in bits, log2 (default: by pattern count) */
     uint32_t warps;            /* consumer warps per CTA, 1..31 (default 24; with a role
-                                  filter: stage-1 warps, default 16, plus up to 4 survivor
+                                  filter: stage-1 warps, default 16, plus up to 6 survivor
                                   warps within 31) */
     uint32_t tile_bytes;       /* text bytes per pipeline tile, multiple of 16, <= 65536
-                                  (default 49152; with a role filter 32768) */
-    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2; with a role
-                                  filter 3) */
+                                  (default 49152) */
+    uint32_t stages;           /* tiles in flight per CTA, 2..8 (default 2) */
     uint32_t ctas_per_sm;      /* resident CTAs per SM (default 1) */
     uint32_t sample;           /* 0: when every pattern has >= 7 bytes and no role filter is
                                   built, scans with a candidate list (rk_scan_device_ws) test
@@ -97,12 +96,16 @@ typedef struct rk_build_opts {
                                   the 4 bytes at p: those bytes stand for the pattern bytes
                                   j..j+3 of a window starting at p - j, either on their own
                                   (shorter patterns) or together with the 4 bytes at p + 4
-                                  (the pattern bytes j+4..j+7).  Step 4 needs every pattern
-                                  to have at least 7 bytes, step 2 at least 4 (at most 64
-                                  patterns of 4 bytes); the builder also declines a set with
-                                  more than one gram per 64 bits of the filter's largest
-                                  size (2^19 bits), where the other filters pass fewer
-                                  windows.  Every scan of the table uses it. */
+                                  (the pattern bytes j+4..j+7).  Step 4 covers patterns
+                                  shorter than 7 bytes with a side set tested at the other
+                                  even positions; both steps take patterns of 4 bytes or more
+                                  (at most 64 of exactly 4).  The builder takes step 4 when
+                                  every pattern has 7 bytes or more (a side set only when
+                                  asked for), else step 2, and declines a set with more than
+                                  one gram per 16 bits of the
+                                  filter's largest size (2^19 bits), or more than 1024
+                                  side-set grams, where the other filters pass fewer windows.
+                                  Every scan of the table uses it. */
 } rk_build_opts;
 
 /* Read-back of a table's shape and launch configuration. */
@@ -124,6 +127,9 @@ typedef struct rk_table_info {
     uint32_t role_filter_log2_bits;    /* its bit set's size (0 without) */
     uint32_t survivor_warps;   /* role filter: warps per CTA that handle the windows stage 1
                                   passes (warps counts the stage-1 warps); 0 without */
+    uint32_t role_side_log2_bits;  /* step-4 role filter over patterns shorter than 7 bytes:
+                                  size of the side set that covers them at the positions
+                                  2 mod 4 (14; 0 without) */
 } rk_table_info;
 
 /* Human-readable text of a status code (static storage). */
@@ -210,8 +216,8 @@ uint64_t rk_scan_workspace_bytes(const rk_table *t, uint64_t n);
  *   d_workspace  at least rk_scan_workspace_bytes(t, n) bytes, 16-byte
  *                aligned, not shared with a call in flight; a smaller,
  *                unaligned or null workspace, a table built with
- *                RK_FILTER_NONE, or one with more than 2^23 distinct q-byte
- *                prefixes (a candidate holds its prefix-map slot in 24 bits)
+ *                RK_FILTER_NONE, or one with more than 2^21 distinct q-byte
+ *                prefixes (a candidate holds its prefix-map slot in 22 bits)
  *                runs rk_scan_device instead.
  * Other arguments, results and errors as rk_scan_device.                    */
 int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,

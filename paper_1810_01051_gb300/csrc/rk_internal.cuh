@@ -101,9 +101,13 @@ struct DevTable {
     // lo brings the roles to bits 31, 30, 29; S also sets bit 28 (both S
     // bits are tested).
     uint32_t rf_step;
-    const uint32_t *rfilter;  // the bit set's shared-memory image
-    uint32_t rfilter_bytes;
+    const uint32_t *rfilter;  // the bit set's shared-memory image (then the side set's)
+    uint32_t rfilter_bytes;   // both images
     uint32_t rf_shift;        // byte address of G's word: (lo >> rf_shift) & ~3
+    // Step 4 with patterns shorter than 7 bytes: byte offset of a side set
+    // (2^14 bits replicated into the 32 banks) tested at the positions 2 mod
+    // 4 for those patterns' grams at offsets 0 and 1 (0: none).
+    uint32_t rf_side_off;
 
     uint32_t n_patterns;
     uint32_t lmin, lmax;

@@ -56,7 +56,8 @@ int launch_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x
 }
 
 bool can_defer(const rk_table *t) {
-    return t->dev.filter_mode != kFilterNone && t->dev.gram_bits <= 64 - kCandSlotShift;
+    return t->dev.filter_mode != kFilterNone &&
+           t->dev.gram_bits <= kCandClassShift - kCandSlotShift;
 }
 
 int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t x_begin,
@@ -81,8 +82,10 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
     // they fit the shared memory sized for the table's tile.
     const uint64_t span = p.mis + x_end - p.u_first;
     const uint64_t max_ctas = (uint64_t)t->sm_count * tu.ctas_per_sm;
-    // (a stage-1 round of a warp: 1 KiB, or 2 KiB with a step-4 role filter)
-    const uint64_t round_bytes = (uint64_t)tu.warps * (t->dev.rf_step == 4 ? 2048u : 1024u);
+    // (a stage-1 round of a warp: 1 KiB, or 2 KiB with a step-4 role filter
+    // without a side set)
+    const uint64_t round_bytes =
+        (uint64_t)tu.warps * (t->dev.rf_step == 4 && !t->dev.rf_side_off ? 2048u : 1024u);
     const uint64_t per_cta = (span + max_ctas - 1) / max_ctas;
     const uint32_t tile = (uint32_t)std::min<uint64_t>(
         tu.tile_bytes, std::max<uint64_t>(round_bytes, (per_cta + round_bytes - 1) / round_bytes *
@@ -111,7 +114,8 @@ int launch_scan_opts(const rk_table *t, const uint8_t *d_text, uint64_t n, uint6
         p.tab.filter_bytes = t->dev.rfilter_bytes;
         p.sv_warps = tu.sv_warps;
         threads = (tu.warps + tu.sv_warps + 1) * 32;
-        e = scan::launch_role(p, grid, threads, sm, stream, t->dev.rf_step);
+        e = scan::launch_role(p, grid, threads, sm, stream, t->dev.rf_step,
+                              t->dev.rf_side_off != 0);
         return e == cudaSuccess ? RK_OK : RK_ECUDA;
     }
     // a deferred scan of a sampled table stages the grams' bit set instead

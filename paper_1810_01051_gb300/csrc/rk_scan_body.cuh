@@ -251,8 +251,33 @@ __device__ __forceinline__ void process_window(const WinCtx &C, const WarpCtx &w
 // prefix-map slot whose lengths apply to a window; the candidate {offset |
 // slot << 40, window bytes 0..7} goes to a global list, and a separate
 // kernel hashes, probes and verifies the whole list 32 candidates per warp
-// (rk_verify.cu), reading longer windows' other bytes from the text.
+// (rk_verify.cu), reading longer windows' other bytes from the text.  With a
+// role filter's side table a candidate also carries a length class.
 constexpr uint32_t kCandSlotShift = 40;          // text offsets are below 2^40
+constexpr uint32_t kCandClassShift = 62;         // slots are below 2^22: two bits for a class
+constexpr uint64_t kCandSlotMask = (1ull << (kCandClassShift - kCandSlotShift)) - 1ull;
+
+// Pattern-length class of a window: every length, or only those from
+// kRfSplit on, or only those below it (a role filter with a side table finds
+// the two kinds of a window through different sampled positions).
+enum LenClass : uint32_t { kLenAll = 0, kLenLong = 1, kLenShort = 2 };
+constexpr uint32_t kRfSplit = 7;
+
+__device__ __forceinline__ bool len_in_class(uint32_t L, uint32_t cls) {
+    return cls == kLenAll || ((L >= kRfSplit) == (cls == kLenLong));
+}
+
+// A candidate's parts: text offset, prefix-map slot, length class.
+__device__ __forceinline__ uint64_t cand_x(uint64_t e) {
+    return e & ((1ull << kCandSlotShift) - 1ull);
+}
+__device__ __forceinline__ uint32_t cand_slot(uint64_t e) {
+    return (uint32_t)((e >> kCandSlotShift) & kCandSlotMask);
+}
+__device__ __forceinline__ uint32_t cand_class(uint64_t e) { return (uint32_t)(e >> kCandClassShift); }
+__device__ __forceinline__ uint64_t cand_pack(uint64_t x, uint32_t slot, uint32_t cls) {
+    return x | ((uint64_t)slot << kCandSlotShift) | ((uint64_t)cls << kCandClassShift);
+}
 constexpr uint32_t kCandBuf = kMatchCap / 2;     // 16-byte candidates in a warp's match buffer
 
 // The prefix-map slot whose lengths apply to a window whose bytes 0..7 are v
@@ -285,7 +310,8 @@ __device__ __forceinline__ int gram_lookup(const WinCtx &C, const Src &src, Pos 
 // (text offset x): A2 hash, A3 probe, A4 verify, A5 emit.
 template <bool DIRECT = false, class Src, class Pos>
 __device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, const Src &src,
-                                           Pos pos, uint64_t x, uint32_t gi) {
+                                           Pos pos, uint64_t x, uint32_t gi,
+                                           uint32_t cls = kLenAll) {
     const GramSlot g = C.s2.grams[gi];
     const bool ext_ok = (g.ext >> ext_bit((uint32_t)(ld8(src, pos) >> (8u * C.q)))) & 1u;
     const uint32_t cnt = g.count & ~kGramShort;
@@ -293,7 +319,7 @@ __device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, co
         const uint32_t L = C.s2.gram_lens[g.first + j];
         if (x + L > C.n) break;  // lengths ascend
         if (L >= C.q + 4 && !ext_ok) break;
-        probe_length<DIRECT>(C, w, src, pos, x, L);
+        if (len_in_class(L, cls)) probe_length<DIRECT>(C, w, src, pos, x, L);
     }
 }
 
@@ -302,8 +328,8 @@ __device__ __forceinline__ void probe_slot(const WinCtx &C, const WarpCtx &w, co
 // candidates).
 __device__ __forceinline__ void cand_overflow(const WinCtx &C, const WarpCtx &w, const uint8_t *buf,
                                               uint64_t u0, uint64_t e) {
-    const uint64_t x = e & ((1ull << kCandSlotShift) - 1ull);
-    probe_slot<true>(C, w, buf, (uint32_t)(x + C.mis - u0), x, (uint32_t)(e >> kCandSlotShift));
+    const uint64_t x = cand_x(e);
+    probe_slot<true>(C, w, buf, (uint32_t)(x + C.mis - u0), x, cand_slot(e), cand_class(e));
 }
 
 // Stage 2a for the window at pos of the tile at u0; a candidate is queued in
@@ -316,7 +342,7 @@ __device__ __forceinline__ void cand_window(const WinCtx &C, const WarpCtx &w, c
     uint64_t v8;
     const int gi = gram_lookup(C, buf, pos, &v8);
     if (gi < 0) return;
-    const ulonglong2 c = make_ulonglong2((ua - C.mis) | ((uint64_t)gi << kCandSlotShift), v8);
+    const ulonglong2 c = make_ulonglong2(cand_pack(ua - C.mis, (uint32_t)gi, kLenAll), v8);
     const uint32_t s = atomicAdd(w.mcount, 1u);
     if (s < kCandBuf) {
         reinterpret_cast<ulonglong2 *>(w.mbuf)[s] = c;
@@ -602,26 +628,47 @@ __device__ __forceinline__ uint32_t rf_probe(uint32_t g, const uint8_t *rfilt, u
     return __funnelshift_r(word, word, lo);
 }
 
+// G's word of a side set (replicated into the 32 banks: the lane reads its
+// own bank's copy), chosen by G's low three bytes, rotated by G's top byte so
+// that the bit pair a gram with that top byte sets sits at bits 31 and 28.
+__device__ __forceinline__ uint32_t rf_side_probe(uint32_t g, const uint8_t *side,
+                                                  uint32_t lane4) {
+    const uint32_t lo = (g & 0x00FFFFFFu) * kRoleMult;
+    const uint32_t word =
+        *reinterpret_cast<const uint32_t *>(side + (((lo >> 16) & 0xFF80u) | lane4));
+    return __funnelshift_r(word, word, g >> 24);
+}
+
+// Kinds of role filter: 2 and 4, the sampling step; 6, step 4 with a side
+// set tested at the positions 2 mod 4.  Kinds 2 and 6 sample every even
+// position of a chunk and share its layout (rf_step_of).
+__host__ __device__ constexpr int rf_step_of(int kind) { return kind == 4 ? 4 : 2; }
+
 // Roles of the sampled positions of one 16-byte chunk (words v; v4: the next
 // chunk's first word), one nibble per position i (bit 3 S, bit 2 L, bit 1 B,
 // bit 0 S's second bit):
-//   STEP 2: positions 2i, i < 8, in nibble 7 - i of the 32-bit result;
-//   STEP 4: positions 4i, i < 4, in nibble 3 - i of the low 16 bits.
-template <int STEP>
+//   kinds 2, 6: positions 2i, i < 8, in nibble 7 - i of the 32-bit result
+//     (kind 6: even i from the main set, odd i from the side set);
+//   kind 4: positions 4i, i < 4, in nibble 3 - i of the low 16 bits.
+template <int KIND>
 __device__ __forceinline__ uint32_t rf_chunk(const uint4 v, uint32_t v4, const uint8_t *rfilt,
-                                             uint32_t rshift) {
+                                             uint32_t rshift, const uint8_t *side,
+                                             uint32_t lane4) {
     const uint32_t wd[5] = {v.x, v.y, v.z, v.w, v4};
     uint32_t a = 0, b = 0;  // two independent accumulators
-    if constexpr (STEP == 2) {
+    if constexpr (rf_step_of(KIND) == 2) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const uint32_t g =
                 (i & 1) ? __funnelshift_r(wd[i >> 1], wd[(i >> 1) + 1], 16) : wd[i >> 1];
-            const uint32_t r = rf_probe(g, rfilt, rshift);
+            const uint32_t r = (KIND == 6 && (i & 1)) ? rf_side_probe(g, side, lane4)
+                                                      : rf_probe(g, rfilt, rshift);
             if (i < 4) a = __funnelshift_l(r, a, 4);  // a = a << 4 | r >> 28
             else b = __funnelshift_l(r, b, 4);
         }
-        return __byte_perm(b, a, 0x5410);  // a << 16 | b
+        const uint32_t acc = __byte_perm(b, a, 0x5410);  // a << 16 | b
+        // a side nibble keeps only S's bits: its other bits carry no role
+        return KIND == 6 ? acc & 0xF9F9F9F9u : acc;
     } else {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -667,17 +714,18 @@ __device__ __forceinline__ uint32_t rf_pos(uint32_t cbase, uint32_t b) {
 // stage 2 (the rest of a longer window read from the text in global memory).
 template <bool DEFER>
 __device__ __forceinline__ void rf_window_g(const WinCtx &C, const WarpCtx &w, const CandList *cc,
-                                            const GText &g, uint64_t ua, uint64_t v8) {
+                                            const GText &g, uint64_t ua, uint64_t v8,
+                                            uint32_t cls) {
     if (ua < C.lo || ua >= C.hi) return;
     const int gi = gram_lookup_v8(C, v8);
     if (gi < 0) return;
     const uint64_t x = ua - C.mis;
     const WText win{g, ua, v8};
     if (!DEFER) {
-        probe_slot(C, w, win, ua, x, (uint32_t)gi);
+        probe_slot(C, w, win, ua, x, (uint32_t)gi, cls);
         return;
     }
-    const ulonglong2 c = make_ulonglong2(x | ((uint64_t)gi << kCandSlotShift), v8);
+    const ulonglong2 c = make_ulonglong2(cand_pack(x, (uint32_t)gi, cls), v8);
     const uint32_t s = atomicAdd(w.mcount, 1u);
     if (s < kCandBuf) {
         reinterpret_cast<ulonglong2 *>(w.mbuf)[s] = c;
@@ -685,7 +733,7 @@ __device__ __forceinline__ void rf_window_g(const WinCtx &C, const WarpCtx &w, c
     }
     const unsigned long long k = atomicAdd(cc->count, 1ull);
     if (k < cc->cap) cc->list[k] = c;
-    else probe_slot<true>(C, w, win, ua, x, (uint32_t)gi);
+    else probe_slot<true>(C, w, win, ua, x, (uint32_t)gi, cls);
 }
 
 // Warp-converged: the warp's buffered candidates to the list with one
@@ -704,8 +752,8 @@ __device__ __forceinline__ void rf_cand_flush(const WinCtx &C, const WarpCtx &w,
             if (base + i < cc.cap) {
                 cc.list[base + i] = c;
             } else {
-                const uint64_t x = c.x & ((1ull << kCandSlotShift) - 1ull);
-                probe_slot<true>(C, w, g, x + C.mis, x, (uint32_t)(c.x >> kCandSlotShift));
+                const uint64_t x = cand_x(c.x);
+                probe_slot<true>(C, w, g, x + C.mis, x, cand_slot(c.x), cand_class(c.x));
             }
         }
     }

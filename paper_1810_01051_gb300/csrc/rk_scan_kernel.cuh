@@ -205,7 +205,7 @@ cudaError_t launch_replicated(const ScanParams &p, uint32_t grid, uint32_t threa
 cudaError_t launch_flat(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                         cudaStream_t st, bool q4, bool samp);
 cudaError_t launch_role(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
-                        cudaStream_t st, uint32_t step);
+                        cudaStream_t st, uint32_t step, bool side);
 
 }  // namespace scan
 }  // namespace rk

@@ -2,7 +2,7 @@
 // specialised.  Per CTA of a persistent grid:
 //   - a producer warp streams tiles plus halo into a ring of shared-memory
 //     stages with 1-D bulk copies (as the other scan kernel does);
-//   - stage-1 warps test every STEP-th position of each staged tile against
+//   - stage-1 warps test every 2nd or 4th position of each staged tile against
 //     the role filter and push the sampled positions that survive (absolute
 //     text positions) into rings in shared memory, one per survivor warp;
 //   - each survivor warp takes its ring's entries 32 at a time and handles the windows
@@ -112,20 +112,24 @@ __device__ __forceinline__ bool rf_slot_wait(volatile uint64_t *ring, uint32_t i
 // last chunk, the next tile's first, read from the halo), from lane 0's next
 // chunk for lane 31, and for lane 31's last chunk (which belongs to another
 // warp) every second gram counts as present.  The sampled positions of
-// chunks [0, nchunks) are tested; each stands for the windows up to STEP - 1
+// chunks [0, nchunks) are tested; each stands for the windows up to 3
 // bytes before it.  A lane with survivors in a round writes one ring entry
-// (its first chunk and candidate mask), reserved with one atomic.  Returns
-// false if a wait for a free ring slot ran out.
-template <int STEP>
+// (its first chunk and candidate mask); the warp reserves its entries with
+// one atomic.  Returns false if a wait for a free ring slot ran out.
+template <int KIND>
 __device__ __forceinline__ bool rf_stage1_tile(const uint8_t *buf, uint64_t u0, uint32_t nchunks,
                                                uint32_t tile, const uint8_t *rfilt,
-                                               uint32_t rshift, uint32_t warp, uint32_t nw,
+                                               uint32_t rshift, uint32_t side_off, uint32_t warp,
+                                               uint32_t nw,
                                                uint32_t lane, volatile uint64_t *ring,
                                                RfRingCtl *rc, uint32_t rsize_log2,
                                                uint64_t timeout_ns) {
     const uint32_t rsize = 1u << rsize_log2;
     volatile RfRingCtl *vc = rc;
+    constexpr int STEP = rf_step_of(KIND);
     constexpr uint32_t NCH = STEP == 2 ? 2 : 4;
+    const uint8_t *side = rfilt + side_off;
+    const uint32_t lane4 = lane << 2;
     constexpr uint32_t kFull = 0xffffffffu;
     const uint32_t lastc = tile / 16u;
     const uint32_t step = nw * 32u * NCH;
@@ -158,7 +162,8 @@ __device__ __forceinline__ bool rf_stage1_tile(const uint8_t *buf, uint64_t u0, 
         }
         uint32_t acc[NCH];
 #pragma unroll
-        for (uint32_t k = 0; k < NCH; ++k) acc[k] = rf_chunk<STEP>(v[k], v4[k], rfilt, rshift);
+        for (uint32_t k = 0; k < NCH; ++k)
+            acc[k] = rf_chunk<KIND>(v[k], v4[k], rfilt, rshift, side, lane4);
         uint32_t m = 0;
 #pragma unroll
         for (uint32_t k = 0; k < NCH; ++k) {
@@ -171,45 +176,56 @@ __device__ __forceinline__ bool rf_stage1_tile(const uint8_t *buf, uint64_t u0, 
         for (uint32_t k = 0; k < NCH; ++k) v[k] = nv[k];
         const uint32_t cbase = c0 + lane;
         c0 += step;
-        if (m) {
-            // one ring entry for the lane's survivors of this round
-            const uint32_t at = atomicAdd(&rc->tail, 1u);
-            if (!rf_room(at + 1u, freed, rsize)) {
-                // the ring is full: wait for its survivor warp
-                const uint64_t t0 = globaltimer_ns();
-                while (!rf_room(at + 1u, vc->freed, rsize)) {
-                    __nanosleep(64);
-                    if (globaltimer_ns() - t0 > timeout_ns) {
-                        ok = false;  // the slot stays unwritten: its consumer gives up
-                        m = 0;
-                        break;
+        // one ring entry per lane with survivors in this round, the warp's
+        // entries reserved with one atomic
+        const uint32_t who = __ballot_sync(kFull, m != 0);
+        if (who) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(&rc->tail, (unsigned int)__popc(who));
+            at = __shfl_sync(kFull, at, 0) + __popc(who & ((1u << lane) - 1u));
+            if (m) {
+                if (!rf_room(at + 1u, freed, rsize)) {
+                    // the ring is full: wait for its survivor warp
+                    const uint64_t t0 = globaltimer_ns();
+                    while (!rf_room(at + 1u, vc->freed, rsize)) {
+                        __nanosleep(64);
+                        if (globaltimer_ns() - t0 > timeout_ns) {
+                            ok = false;  // the slot stays unwritten: its consumer gives up
+                            m = 0;
+                            break;
+                        }
                     }
                 }
+                if (m)
+                    ring[at & (rsize - 1u)] = rf_lap_bits(at, rsize_log2) |
+                                              (((u0 >> 4) + cbase) << 16) | rf_mask16<STEP>(m);
             }
-            if (m)
-                ring[at & (rsize - 1u)] = rf_lap_bits(at, rsize_log2) |
-                                          (((u0 >> 4) + cbase) << 16) | rf_mask16<STEP>(m);
         }
     }
     return __all_sync(kFull, ok);
 }
 
 // The windows a surviving sampled position up (buffer position) stands
-// for: up - j, j < STEP, each handled by rf_window_g; the 16 bytes from the
-// word at or before the first of them hold every window's bytes 0..7 and
-// are read with four independent loads.
-template <int STEP, bool DEFER>
+// for, each handled by rf_window_g: up - j for j < the step; kind 6: at a
+// main position (0 mod 4) j = 0, 1 for every pattern length and j = 2, 3
+// for lengths from kRfSplit on, at a side position (2 mod 4) j = 0, 1 for
+// the shorter lengths.  The 16 bytes from the word at or before the first of
+// them hold every window's bytes 0..7 and are read with four independent
+// loads.
+template <int KIND, bool DEFER>
 __device__ __forceinline__ void rf_position(const WinCtx &C, const WarpCtx &w, const CandList *cc,
                                             const GText &g, uint64_t up) {
-    const uint64_t first = up >= (uint64_t)(STEP - 1) ? up - (STEP - 1) : 0;
+    const bool side = KIND == 6 && (up & 3u) != 0;
+    const uint32_t nwin = KIND == 2 || side ? 2u : 4u;
+    const uint64_t first = up >= nwin - 1 ? up - (nwin - 1) : 0;
     const uint64_t a = first & ~uint64_t(3), last = g.end - 4;
     const uint32_t *tw = reinterpret_cast<const uint32_t *>(g.base);
     uint32_t wd[4];
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) wd[i] = __ldg(tw + (min(a + 4u * i, last) >> 2));
 #pragma unroll
-    for (uint32_t j = 0; j < (uint32_t)STEP; ++j) {
-        if (up < j) continue;
+    for (uint32_t j = 0; j < 4; ++j) {
+        if (j >= nwin || up < j) continue;
         const uint64_t ua = up - j;
         const uint32_t d = (uint32_t)(ua - a);  // 0..6
         const uint32_t s8 = (d & 3u) * 8u;
@@ -217,7 +233,8 @@ __device__ __forceinline__ void rf_position(const WinCtx &C, const WarpCtx &w, c
                        w2 = d >= 4 ? wd[3] : wd[2];
         const uint64_t v8 =
             ((uint64_t)__funnelshift_r(w1, w2, s8) << 32) | __funnelshift_r(w0, w1, s8);
-        rf_window_g<DEFER>(C, w, cc, g, ua, v8);
+        const uint32_t cls = KIND != 6 ? kLenAll : side ? kLenShort : j < 2 ? kLenAll : kLenLong;
+        rf_window_g<DEFER>(C, w, cc, g, ua, v8, cls);
     }
 }
 
@@ -235,7 +252,7 @@ struct RfXBuf {
 // (handled where the set-aside buffer is full); full rounds of set-aside
 // positions follow as 32 gather.  Flushes its buffered candidates (DEFER)
 // or matches as they fill and at the end.  Returns false if a wait ran out.
-template <int STEP, bool DEFER>
+template <int KIND, bool DEFER>
 __device__ __forceinline__ bool rf_survivor_warp(const WinCtx &C, const WarpCtx &w,
                                                  const CandList *cc, const GText &g,
                                                  volatile uint64_t *ring, RfRingCtl *rc,
@@ -295,10 +312,10 @@ __device__ __forceinline__ bool rf_survivor_warp(const WinCtx &C, const WarpCtx 
                     const uint32_t c = __ffs(mask) - 1u;
                     mask &= mask - 1u;
                     const uint32_t at = atomicAdd(xb.count, 1u);
-                    if (at < kRfXCap) xb.pos[at] = rf_mask_pos<STEP>(base, c);
-                    else rf_position<STEP, DEFER>(C, w, cc, g, rf_mask_pos<STEP>(base, c));
+                    if (at < kRfXCap) xb.pos[at] = rf_mask_pos<rf_step_of(KIND)>(base, c);
+                    else rf_position<KIND, DEFER>(C, w, cc, g, rf_mask_pos<rf_step_of(KIND)>(base, c));
                 }
-                rf_position<STEP, DEFER>(C, w, cc, g, rf_mask_pos<STEP>(base, c0));
+                rf_position<KIND, DEFER>(C, w, cc, g, rf_mask_pos<rf_step_of(KIND)>(base, c0));
             } else {
                 ok = false;
             }
@@ -313,7 +330,7 @@ __device__ __forceinline__ bool rf_survivor_warp(const WinCtx &C, const WarpCtx 
         __syncwarp();
         // set-aside positions, a full round of 32 at a time
         for (uint32_t xn = *reinterpret_cast<volatile uint32_t *>(xb.count); xn >= 32u; xn -= 32u) {
-            rf_position<STEP, DEFER>(C, w, cc, g, xb.pos[xn - 32u + lane]);
+            rf_position<KIND, DEFER>(C, w, cc, g, xb.pos[xn - 32u + lane]);
             __syncwarp();
             if (lane == 0) *reinterpret_cast<volatile uint32_t *>(xb.count) = xn - 32u;
         }
@@ -327,7 +344,7 @@ __device__ __forceinline__ bool rf_survivor_warp(const WinCtx &C, const WarpCtx 
     }
     // the set-aside positions left
     const uint32_t xn = *reinterpret_cast<volatile uint32_t *>(xb.count);
-    if (lane < xn) rf_position<STEP, DEFER>(C, w, cc, g, xb.pos[lane]);
+    if (lane < xn) rf_position<KIND, DEFER>(C, w, cc, g, xb.pos[lane]);
     __syncwarp();
     if (DEFER) rf_cand_flush(C, w, *cc, g, lane);
     else flush(w, lane);
@@ -339,7 +356,7 @@ __device__ __forceinline__ bool rf_survivor_warp(const WinCtx &C, const WarpCtx 
 // warps, then the producer warp.  S2S: survivor tables staged in shared
 // memory.  DEFER: survivors stop after the prefix-map lookup and go to the
 // candidate list (verified by rk_verify_kernel).
-template <int STEP, int MAXW, bool S2S, bool DEFER>
+template <int KIND, int MAXW, bool S2S, bool DEFER>
 __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     rk_scan_rf_kernel(const __grid_constant__ ScanParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -429,10 +446,12 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
             const uint64_t u0 = P.u_first + t * P.tile;
             // the chunks holding the sampled positions of this tile's windows
             // (a window belongs to the tile of its sampled position); in the
-            // last tile they reach up to STEP - 1 bytes past its last window
-            const uint64_t wend = hi <= u0 + P.tile ? hi + (STEP - 1) : u0 + P.tile;
+            // last tile they reach up to 1 (kind 2) or 3 bytes past its last
+            // window
+            const uint64_t wend = hi <= u0 + P.tile ? hi + (KIND == 2 ? 1 : 3) : u0 + P.tile;
             const uint32_t nchunks = (uint32_t)((wend - u0 + 15) / 16);
-            if (!rf_stage1_tile<STEP>(buf, u0, nchunks, P.tile, rfilt, P.tab.rf_shift, warp, nw1,
+            if (!rf_stage1_tile<KIND>(buf, u0, nchunks, P.tile, rfilt, P.tab.rf_shift,
+                                      P.tab.rf_side_off, warp, nw1,
                                       lane, ring + (warp % nsv) * rsize, rctl + warp % nsv, rlog,
                                       P.timeout_ns) &&
                 lane == 0)
@@ -469,17 +488,17 @@ __global__ void __launch_bounds__((MAXW + 1) * 32, 1)
     const GText g{P.base, P.n16};
     uint8_t *xraw = smem + lay.xbuf_off + sw * (kRfXCap * 8 + 16);
     const RfXBuf xb{reinterpret_cast<uint64_t *>(xraw), reinterpret_cast<uint32_t *>(xraw + kRfXCap * 8)};
-    if (!rf_survivor_warp<STEP, DEFER>(C, w, &P.cand, g, ring + sw * rsize, rctl + sw, rlog, ctl,
+    if (!rf_survivor_warp<KIND, DEFER>(C, w, &P.cand, g, ring + sw * rsize, rctl + sw, rlog, ctl,
                                        xb, nw1, lane, P.timeout_ns) &&
         lane == 0)
         P.info[1] = RK_ETIMEOUT;
 }
 
-template <int STEP, bool DEFER, int MAXW>
+template <int KIND, bool DEFER, int MAXW>
 cudaError_t launch_rf_w(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                         cudaStream_t st) {
-    auto fn = p.s2_smem ? rk_scan_rf_kernel<STEP, MAXW, true, DEFER>
-                        : rk_scan_rf_kernel<STEP, MAXW, false, DEFER>;
+    auto fn = p.s2_smem ? rk_scan_rf_kernel<KIND, MAXW, true, DEFER>
+                        : rk_scan_rf_kernel<KIND, MAXW, false, DEFER>;
     // raise the dynamic shared-memory limit once per device and size
     static thread_local int seen_dev[2] = {-1, -1};
     static thread_local uint32_t seen_smem[2] = {0, 0};
@@ -497,13 +516,13 @@ cudaError_t launch_rf_w(const ScanParams &p, uint32_t grid, uint32_t threads, ui
     return cudaGetLastError();
 }
 
-template <int STEP, bool DEFER>
+template <int KIND, bool DEFER>
 cudaError_t launch_rf_d(const ScanParams &p, uint32_t grid, uint32_t threads, uint32_t smem,
                         cudaStream_t st) {
     const uint32_t nw = p.warps + p.sv_warps;
-    if (nw <= 16) return launch_rf_w<STEP, DEFER, 16>(p, grid, threads, smem, st);
-    if (nw <= 24) return launch_rf_w<STEP, DEFER, 24>(p, grid, threads, smem, st);
-    return launch_rf_w<STEP, DEFER, 31>(p, grid, threads, smem, st);
+    if (nw <= 16) return launch_rf_w<KIND, DEFER, 16>(p, grid, threads, smem, st);
+    if (nw <= 24) return launch_rf_w<KIND, DEFER, 24>(p, grid, threads, smem, st);
+    return launch_rf_w<KIND, DEFER, 31>(p, grid, threads, smem, st);
 }
 
 }  // namespace scan

@@ -142,32 +142,71 @@ bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_
 // set of 2^bits bits.  Role S sets two bits of the gram's word (at lo + 31
 // and lo + 28, the slot of a fourth role), and the scan asks for both, so a
 // text gram that is no key passes as S about as often as two set bits line
-// up, like L with B.  Step 4 needs every pattern to have at least 7 bytes.
-// Step 2 needs at least 5, or 4 bytes: a 4-byte pattern P has no gram at
-// offset 1, so for an occurrence at an odd x the gram at p = x + 1 holds
-// P[1..4) and one text byte; every such gram (256 of them) gets role S.
-// Returns false when the patterns do not allow the step or the set would be
+// up, like L with B.  Step 2 needs every pattern to have at least 5 bytes,
+// or 4: a 4-byte pattern P has no gram at offset 1, so for an occurrence at
+// an odd x the gram at p = x + 1 holds P[1..4) and one text byte; every such
+// gram (256 of them) gets role S.  Step 4 needs at least 7 bytes, or a side
+// table: the patterns shorter than kRfSplit (7) go into the main set only
+// at offsets 0 and 1 (their windows at positions 0 and 3 mod 4), and into a
+// small set tested at the positions 2 mod 4 (*side), where the same offsets
+// find their windows at positions 2 and 1 mod 4; the scan then looks at
+// windows 2 and 3 bytes before a main position only for longer patterns.
+// The side set (2^14 bits, replicated) picks a word by a gram's low three
+// bytes and the bit pair by its top byte (side_word).
+// Returns false when the patterns do not allow the step or a set would be
 // too dense (more than one key per 16 bits at the largest size).
 constexpr uint32_t kRoleMaxLog2Bits = 19;   // 64 KiB of shared memory
-constexpr uint32_t kRoleMaxWild = 64;       // 4-byte patterns a step-2 filter takes
+constexpr uint32_t kRoleMaxWild = 64;       // 4-byte patterns a filter takes
 constexpr uint32_t kRoleBitsPerKey = 16;    // least bits per key
-constexpr uint32_t kRfSurvivorWarps = 4;    // survivor warps of the role-filter scan kernel
+constexpr uint32_t kRfSurvivorWarps = 6;    // survivor warps of the role-filter scan kernel
+constexpr uint32_t kRfSplitLen = 7;         // shorter patterns use the side table (step 4)
+constexpr uint32_t kSideWords = 512;        // side table: 2^14 bits, replicated into 32 banks
+constexpr uint32_t kSideMaxKeys = 1024;
+
+// The grams of pattern p (length L) at offsets 0 and 1 (or its wildcard
+// grams), role S, appended to keys.
+void short_keys(const uint8_t *p, uint32_t L,
+                std::vector<std::pair<uint32_t, uint32_t>> *keys) {
+    keys->emplace_back(prefix_key(p, 4), 0u);
+    if (L >= 5) {
+        keys->emplace_back(prefix_key(p + 1, 4), 0u);
+    } else {
+        const uint32_t g3 = prefix_key(p + 1, 3);
+        for (uint32_t c = 0; c < 256; ++c) keys->emplace_back(g3 | (c << 24), 0u);
+    }
+}
+
+// The side set's word for a gram: chosen by its low three bytes (so that the
+// wildcard grams of a 4-byte pattern, P[1..4) and any fourth byte, share one
+// word), the bit pair by its top byte.
+uint32_t side_word(uint32_t g) { return ((g & 0x00FFFFFFu) * kRoleMult) >> 23; }
 
 bool make_role_filter(const uint8_t *patterns, const std::vector<uint64_t> &src_off,
                       const std::vector<uint32_t> &plen, uint32_t step,
-                      std::vector<uint32_t> *img, uint32_t *log2_bits) {
+                      std::vector<uint32_t> *img, uint32_t *log2_bits,
+                      std::vector<uint32_t> *side) {
     const uint32_t k = (uint32_t)plen.size();
     uint32_t lmin = UINT32_MAX, n4 = 0;
     for (uint32_t L : plen) {
         lmin = std::min(lmin, L);
         n4 += L == 4;
     }
-    if (step == 4 ? lmin < 7 : (lmin < 4 || n4 > kRoleMaxWild)) return false;
+    side->clear();
+    if (lmin < 4 || n4 > kRoleMaxWild) return false;
+    const bool with_side = step == 4 && lmin < kRfSplitLen;
     std::vector<std::pair<uint32_t, uint32_t>> keys;  // (gram, role 0 S / 1 L / 2 B)
+    std::vector<std::pair<uint32_t, bool>> skeys;      // side set: (gram, any top byte)
     keys.reserve((size_t)k * step * 2 + (size_t)n4 * 256);
     for (uint32_t i = 0; i < k; ++i) {
         const uint8_t *p = patterns + src_off[i];
         const uint32_t L = plen[i];
+        if (with_side && L < kRfSplitLen) {
+            short_keys(p, L, &keys);
+            skeys.emplace_back(prefix_key(p, 4), false);
+            if (L >= 5) skeys.emplace_back(prefix_key(p + 1, 4), false);
+            else skeys.emplace_back(prefix_key(p + 1, 3), true);
+            continue;
+        }
         for (uint32_t j = 0; j < step; ++j) {
             if (j + 4 <= L) {
                 const bool longer = L >= j + 8;  // a second gram follows
@@ -179,6 +218,7 @@ bool make_role_filter(const uint8_t *patterns, const std::vector<uint64_t> &src_
             }
         }
     }
+    if (skeys.size() > kSideMaxKeys) return false;
     const uint64_t nk = keys.size();
     const uint32_t bits =
         std::min<uint32_t>(kRoleMaxLog2Bits, std::max<uint32_t>(15, ceil_log2(nk * 512)));
@@ -190,6 +230,20 @@ bool make_role_filter(const uint8_t *patterns, const std::vector<uint64_t> &src_
         uint32_t &word = (*img)[lo >> (32 - wbits)];
         word |= 1u << ((lo + 31u - kr.second) & 31u);
         if (kr.second == 0) word |= 1u << ((lo + 28u) & 31u);  // S's second bit
+    }
+    if (with_side) {
+        // word w of the side set at byte (w << 7) | (bank << 2), every bank a
+        // copy; a gram's bits at its top byte + 31 and + 28 (mod 32), a
+        // wildcard gram's every bit
+        std::vector<uint32_t> bm(kSideWords, 0u);
+        for (const auto &kw : skeys) {
+            const uint32_t t = kw.first >> 24;
+            bm[side_word(kw.first)] |=
+                kw.second ? 0xFFFFFFFFu : (1u << ((t + 31u) & 31u)) | (1u << ((t + 28u) & 31u));
+        }
+        side->resize((size_t)kSideWords * 32);
+        for (uint32_t w = 0; w < kSideWords; ++w)
+            for (uint32_t b = 0; b < 32; ++b) (*side)[(size_t)w * 32 + b] = bm[w];
     }
     *log2_bits = bits;
     return true;
@@ -267,14 +321,18 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
         return RK_EINVAL;
 
     // ---- role filter: sampled grams with their roles ------------------------
-    std::vector<uint32_t> rimg;
+    std::vector<uint32_t> rimg, rside;
     uint32_t rstep = 0, rbits = 0;
     // chosen by the builder only when the prefilter is too (RK_FILTER_AUTO)
     const bool role_ok = role_opt > 1 || (role_opt == 0 && filter_opt == RK_FILTER_AUTO);
     if (role_ok && mode != kFilterNone && q == 4 && k > 0) {
         for (uint32_t step : {4u, 2u}) {
             if (role_opt > 1 && role_opt != step) continue;
-            if (make_role_filter(patterns, src_off, plen, step, &rimg, &rbits)) {
+            // the builder's own choice takes step 4 only without a side set:
+            // with one, every main-position survivor stands for four windows
+            // of survivor-warp work, and step 2 measured faster
+            if (role_opt == 0 && step == 4 && lmin < kRfSplitLen) continue;
+            if (make_role_filter(patterns, src_off, plen, step, &rimg, &rbits, &rside)) {
                 rstep = step;
                 break;
             }
@@ -360,7 +418,8 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     size_t o_lens = b.add(lengths.size() * 4 + 4);
     size_t o_smap = b.add(smap.size() * sizeof(SampSlot) + 8);
     size_t o_sfilter = b.add(simg.size() * 4 + 16);  // after the survivor tables: not staged with them
-    size_t o_rfilter = b.add(rimg.size() * 4 + 16);
+    // the side set right after the main one: the scan stages both with one copy
+    size_t o_rfilter = b.add((rimg.size() + rside.size()) * 4 + 16);
     b.add(0);  // the blob ends on a 256-byte boundary: whole 16-byte copies stay inside
     uint8_t *hb = b.bytes.data();
     if (!fimg.empty()) memcpy(hb + o_filter, fimg.data(), fimg.size() * 4);
@@ -376,6 +435,7 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     if (!smap.empty()) memcpy(hb + o_smap, smap.data(), smap.size() * sizeof(SampSlot));
     if (!simg.empty()) memcpy(hb + o_sfilter, simg.data(), simg.size() * 4);
     if (!rimg.empty()) memcpy(hb + o_rfilter, rimg.data(), rimg.size() * 4);
+    if (!rside.empty()) memcpy(hb + o_rfilter + rimg.size() * 4, rside.data(), rside.size() * 4);
 
     if (b.bytes.size() - o_grams > 0xFFFFFFFFull) return RK_EINVAL;  // tables above 4 GiB
     TableBlob &tb = *out;
@@ -410,7 +470,8 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
     d.sfilter_mask = smask_addr;
     d.smap_bits = smap_bits;
     d.rf_step = rstep;
-    d.rfilter_bytes = (uint32_t)(rimg.size() * 4);
+    d.rfilter_bytes = (uint32_t)((rimg.size() + rside.size()) * 4);
+    d.rf_side_off = rside.empty() ? 0u : (uint32_t)(rimg.size() * 4);
     d.rf_shift = rstep ? 30 - (rbits - 5) : 0;
     d.s2_bytes = (uint32_t)(o_sfilter - o_grams);
     tb.n_grams = D;
@@ -483,26 +544,23 @@ int read_opts(const uint8_t *patterns, const uint32_t *lens, uint32_t k,
     return RK_OK;
 }
 
-// Host part of rk_build: build the host image of the table and pick the
-// launch shape for a device with smem_optin bytes of opt-in shared memory per
-// block.  No CUDA call.
-int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const Opts &o,
-               uint32_t smem_optin, TableBlob *tb, Tuning *tune) {
-    const uint32_t cps = o.cps;
-    // room for the static shared memory of each CTA
-    if (smem_optin / cps <= 1024) return RK_EINVAL;
+constexpr int kNoRoom = -1;  // plan_with: the shared memory cannot hold the pipeline
 
+// plan_table with one role-filter option.
+int plan_with(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const Opts &o,
+              uint32_t role_opt, uint32_t smem_optin, TableBlob *tb, Tuning *tune) {
+    const uint32_t cps = o.cps;
     int rc = build_blob(patterns, lens, k, o.base_log2, o.filter, o.filter_log2_bits, o.sample,
-                        o.role, tb);
+                        role_opt, tb);
     if (rc) return rc;
     const bool role = tb->meta.rf_step != 0;
-    // Defaults.  Prefix filter: 24 warps, 48 KiB tiles (two 24 KiB rounds of
-    // 24 warps), two in flight.  Role filter: 16 stage-1 warps, 32 KiB tiles
-    // (two 16 KiB rounds), three in flight, and kRfSurvivorWarps survivor
-    // warps (fewer when the stage-1 warps leave less room under 31).
+    // Defaults: 48 KiB tiles, two in flight; 24 warps with the prefix filter
+    // (two 24 KiB rounds each), with a role filter 16 stage-1 warps (three
+    // 16 KiB rounds) and kRfSurvivorWarps survivor warps (fewer when the
+    // stage-1 warps leave less room under 31).
     uint32_t warps = o.warps ? o.warps : (role ? 16u : 24u);
-    uint32_t tile = o.tile ? o.tile : (role ? 32768u : 49152u);
-    uint32_t stages = o.stages ? o.stages : (role ? 3u : 2u);
+    uint32_t tile = o.tile ? o.tile : 49152u;
+    uint32_t stages = o.stages ? o.stages : 2u;
     uint32_t sv = 0;
     if (role) {
         sv = std::min<uint32_t>(kRfSurvivorWarps, std::max<uint32_t>(1, 31 - warps));
@@ -540,12 +598,30 @@ int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const 
     while (bytes > limit) {
         if (stages > 2) --stages;
         else if (tile > 4 * halo && tile > 4096) tile /= 2;
-        else return RK_EINVAL;
+        else return kNoRoom;
         tile = tile / 16 * 16;
         bytes = total(s2, stages, tile);
     }
     *tune = Tuning{warps, tile, stages, cps, halo, s2, bytes, sv};
     return RK_OK;
+}
+
+// Host part of rk_build: build the host image of the table and pick the
+// launch shape for a device with smem_optin bytes of opt-in shared memory per
+// block.  When the builder chooses the stage-1 filter and the shared memory
+// cannot hold its pipeline, the next choice is tried: step 2, then no role
+// filter.  No CUDA call.
+int plan_table(const uint8_t *patterns, const uint32_t *lens, uint32_t k, const Opts &o,
+               uint32_t smem_optin, TableBlob *tb, Tuning *tune) {
+    // room for the static shared memory of each CTA
+    if (smem_optin / o.cps <= 1024) return RK_EINVAL;
+    const uint32_t tries[3] = {o.role, 2u, 1u};
+    const uint32_t n = o.role == 0 ? 3 : 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        const int rc = plan_with(patterns, lens, k, o, tries[i], smem_optin, tb, tune);
+        if (rc != kNoRoom) return rc;
+    }
+    return RK_EINVAL;
 }
 
 rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
@@ -579,6 +655,7 @@ rk_table_info make_info(const DevTable &d, const Tuning &tune, uint32_t n_grams,
     r.sample_filter_log2_bits = sfilter_log2_bits;
     r.role_step = d.rf_step;
     r.role_filter_log2_bits = rfilter_log2_bits;
+    r.role_side_log2_bits = d.rf_side_off ? 14u : 0u;
     r.survivor_warps = tune.sv_warps;
     return r;
 }

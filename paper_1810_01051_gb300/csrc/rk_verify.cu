@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(kVerifyThreads)
         const uint64_t i = i0 + lane;
         if (i < nc) {
             const ulonglong2 c = P.list[i];
-            const uint64_t x = c.x & ((1ull << kCandSlotShift) - 1ull);
+            const uint64_t x = cand_x(c.x);
             const WText win{P.text, x + P.mis, c.y};
-            probe_slot(C, w, win, x + P.mis, x, (uint32_t)(c.x >> kCandSlotShift));
+            probe_slot(C, w, win, x + P.mis, x, cand_slot(c.x), cand_class(c.x));
         }
         __syncwarp();
         if (*reinterpret_cast<volatile uint32_t *>(w.mcount) >= kMatchCap - 32) flush(w, lane);

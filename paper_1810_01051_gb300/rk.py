@@ -70,7 +70,8 @@ class TableInfo(ctypes.Structure):
         "ctas_per_sm", "halo_bytes", "smem_bytes", "sm_count", "device", "s2_smem_bytes")] + [
         ("device_bytes", ctypes.c_uint64)] + [
         (n, ctypes.c_uint32) for n in ("sample_step", "sample_filter_log2_bits", "role_step",
-                                       "role_filter_log2_bits", "survivor_warps")]
+                                       "role_filter_log2_bits", "survivor_warps",
+                                       "role_side_log2_bits")]
 
 
 class BatchOpts(ctypes.Structure):

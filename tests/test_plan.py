@@ -54,9 +54,9 @@ def test_pattern_statistics(name):
         assert info[key] == val, key
     assert info["base_log2"] == 8
     if info["role_step"]:
-        # role filter: 16 stage-1 warps, 4 survivor warps, 32 KiB tiles, three stages
-        assert (info["warps"], info["survivor_warps"]) == (16, 4)
-        assert info["tile_bytes"] <= 32768 and info["stages"] <= 3
+        # role filter: 16 stage-1 warps, 6 survivor warps, 48 KiB tiles, two stages
+        assert (info["warps"], info["survivor_warps"]) == (16, 6)
+        assert info["tile_bytes"] <= 49152 and info["stages"] == 2
     else:
         assert info["warps"] == 24 and info["survivor_warps"] == 0
     assert info["sm_count"] == 0 and info["device"] == 0xFFFFFFFF
@@ -90,19 +90,27 @@ def role_keys(patterns, step):
     """Role-filter keys for sampling step `step` counted in Python: per
     pattern, the gram at each offset j < step (and the one 4 bytes on when the
     pattern has j + 8 bytes), or for a 4-byte pattern at j = 1 the 256 grams
-    P[1..4) + any byte; None when the step does not apply."""
+    P[1..4) + any byte.  Step 4 over patterns shorter than 7 bytes gives those
+    only their grams at offsets 0 and 1, in the main set and in a side set
+    of at most 1024 grams.  None when the step does not apply."""
     lens = [len(p) for p in patterns]
-    if step == 4 and min(lens) < 7:
+    if min(lens) < 4 or sum(L == 4 for L in lens) > 64:
         return None
-    if step == 2 and (min(lens) < 4 or sum(L == 4 for L in lens) > 64):
-        return None
-    n = 0
+    side = step == 4 and min(lens) < 7
+    n = ns = 0
     for L in lens:
+        if side and L < 7:
+            k = 2 if L >= 5 else 257
+            n += k
+            ns += k
+            continue
         for j in range(step):
             if j + 4 <= L:
                 n += 2 if L >= j + 8 else 1
             else:
                 n += 256
+    if ns > 1024:
+        return None
     return n
 
 
@@ -116,6 +124,8 @@ def role_rule(patterns, role_step=0, filter=rk.RK_FILTER_AUTO):
     for step in (4, 2):
         if role_step not in (0, step):
             continue
+        if role_step == 0 and step == 4 and min(len(p) for p in patterns) < 7:
+            continue  # the builder's own choice takes no side set
         nk = role_keys(patterns, step)
         if nk is None:
             continue
@@ -131,6 +141,8 @@ def test_sampling_rule(name):
     info = rk.rk_plan(pats)
     step, bits = role_rule(pats)
     assert (info["role_step"], info["role_filter_log2_bits"]) == (step, bits)
+    want_side = 0  # only a forced step 4 takes a side set
+    assert info["role_side_log2_bits"] == want_side
     none = rk.rk_plan(pats, role_step=1)
     assert none["role_step"] == 0 and none["role_filter_log2_bits"] == 0
     for forced in (2, 4):
@@ -158,13 +170,16 @@ def test_sampling_rule(name):
 
 def test_role_filter_choice():
     """The workloads' sets take the filter the rule predicts: a Zipf set (a
-    few 4-byte patterns) step 2 at 2^19 bits, the DNA set step 4, 2,000
+    few patterns under 7 bytes) step 2 (step 4 with a side set when asked
+    for), the DNA set step 4, 2,000
     signature patterns (about 16,000 role keys) step 4, the full 10,000 (about
     79,000) none; patterns below 4 bytes, RK_FILTER_NONE, or more than 64
     four-byte patterns rule it out."""
     sets = pattern_sets()
     z = rk.rk_plan(sets["zipf"])
-    assert (z["role_step"], z["role_filter_log2_bits"]) == (2, 19)
+    assert (z["role_step"], z["role_filter_log2_bits"], z["role_side_log2_bits"]) == (2, 19, 0)
+    z4 = rk.rk_plan(sets["zipf"], role_step=4)
+    assert (z4["role_step"], z4["role_side_log2_bits"]) == (4, 14)
     assert rk.rk_plan(sets["dna"])["role_step"] == 4
     assert rk.rk_plan(sets["signature"])["role_step"] == 4
     big = make_config(2, n=1 << 16, k=10000).patterns
@@ -174,6 +189,7 @@ def test_role_filter_choice():
     many4 = [bytes([65 + i % 26, 66 + i // 26, 67, 68]) for i in range(65)]
     assert rk.rk_plan(many4)["role_step"] == 0
     assert rk.rk_plan(many4[:64])["role_step"] == 2
+    assert rk.rk_plan(many4[:3], role_step=4)["role_side_log2_bits"] == 14
     with pytest.raises(rk.RkError):
         rk.rk_plan(sets["zipf"], role_step=3)
 
@@ -198,8 +214,8 @@ def test_shared_memory_fits_every_request():
         assert 2 <= info["stages"] <= opts["stages"]
         assert info["tile_bytes"] <= opts["tile_bytes"]
         if info["role_step"]:
-            # stage-1 warps plus 1..4 survivor warps within 31
-            sv = min(4, max(1, 31 - opts["warps"]))
+            # stage-1 warps plus 1..6 survivor warps within 31
+            sv = min(6, max(1, 31 - opts["warps"]))
             assert info["survivor_warps"] == sv
             assert info["warps"] == min(opts["warps"], 31 - sv)
         else:
