@@ -39,11 +39,13 @@ UNIT = "GB/s"
 WORKLOAD = "zipf_text_1GiB_100_patterns_len4-32_density1e-6"
 # the sources the scan kernel is compiled from (the profile records their hash)
 SCAN_SRCS = [os.path.join(ROOT, "paper_1810_01051_gb300", "csrc", f)
-             for f in ("rk_scan.cu", "rk_scan_kernel.cuh", "rk_scan_k_role.cu", "rk_scan_body.cuh",
-                       "rk_layout.cuh", "rk_internal.cuh", "rk_verify.cu", "rk_sortws.cuh",
-                       "rk_table.cu")]
+             for f in ("rk_scan.cu", "rk_scan_kernel.cuh", "rk_scan_rf.cuh", "rk_scan_k_role.cu",
+                       "rk_scan_body.cuh", "rk_layout.cuh", "rk_internal.cuh", "rk_verify.cu",
+                       "rk_sortws.cuh", "rk_table.cu")]
 PROFILE = os.path.join(ROOT, "profiles", "rk_scan_zipf_1GiB.md")
+PROFILE_SIG = os.path.join(ROOT, "profiles", "rk_scan_signature_4GiB.md")
 CPU_SAMPLE_PER_CORE = 8 << 20   # bytes per core for the oracle baseline
+SIG_CPU_SAMPLE_PER_CORE = 2 << 20  # the same on the signature set
 SLICE_HALO_NOTE = "each slice carries (longest pattern - 1) extra bytes"
 
 
@@ -115,7 +117,8 @@ def read_profile():
         return None
     out = {}
     for key in ("dram_bytes_per_full_launch", "tile_scan_alu_pipe_frac",
-                "tile_scan_fmaheavy_pipe_frac", "tile_scan_issue_active_frac"):
+                "tile_scan_fmaheavy_pipe_frac", "tile_scan_issue_active_frac",
+                "tile_scan_warp_inst_per_byte"):
         m = re.search(key + r":\s*([0-9.eE+]+)", txt)
         out[key] = float(m.group(1)) if m else None
     return out
@@ -163,6 +166,105 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sms)}
+
+
+# ---------------------------------------------------------------- scan step
+
+class StepBuffers:
+    """Output and workspace for one table and text, sized from one probe
+    search: the sort's scratch first, the deferred scan's candidate list
+    after it."""
+
+    def __init__(self, torch, rk, table, d_text, n, dev, st, cap=1 << 22):
+        self.scan_b = rk.rk_scan_workspace_bytes(table, n)
+        self.info = torch.zeros(2, dtype=torch.int64, device=dev)
+        while True:
+            self.keys = torch.empty(cap, dtype=torch.int64, device=dev)
+            self.wsb = rk.rk_workspace_bytes(table, cap)
+            self.ws = torch.empty(self.wsb + self.scan_b, dtype=torch.uint8, device=dev)
+            rk.rk_search_device(table, d_text, n, self.keys, cap, self.info, self.ws,
+                                self.wsb + self.scan_b, st)
+            st.synchronize()
+            m, status = (int(v) for v in self.info.cpu().tolist())
+            if status != rk.RK_OK:
+                raise RuntimeError(f"search failed: {rk.strerror(status)}")
+            if m <= cap:
+                break
+            cap = m + 1024
+        self.cap, self.m = cap, m
+        self.sws = self.ws[self.wsb:]
+        self.scan_kernels = rk.rk_scan_launches(table, n, self.scan_b)
+        self.sort_kernels = rk.rk_sort_launches(table, n, cap)
+
+    def candidates(self, torch):
+        """Candidate windows the last deferred tile scan listed."""
+        return int(self.sws[:8].view(torch.int64)[0].item()) if self.scan_kernels == 2 else 0
+
+
+def scan_sort(rk, table, d_text, n, b, st, ev=None):
+    """One step: tile scan (+ verification) and sort; `ev` = four events
+    recorded before the tile scan, between it and the verification kernel,
+    before the sort and after it."""
+    if ev:
+        ev[0].record(st)
+        rk.rk_scan_device_ws_split(table, d_text, n, b.keys, b.cap, b.info, b.sws, b.scan_b, st,
+                                   ev[1])
+        ev[2].record(st)
+    else:
+        rk.rk_scan_device_ws(table, d_text, n, b.keys, b.cap, b.info, b.sws, b.scan_b, st)
+    rk.rk_sort_device(table, n, b.keys, b.cap, b.info, b.ws, b.wsb, st)
+    if ev:
+        ev[3].record(st)
+
+
+def new_events(torch, k):
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k)]
+    return evs
+
+
+def create_events(evs, st):
+    """Record every event once so that each exists before its handle is passed
+    to the library."""
+    for e in evs:
+        e[1].record(st)
+
+
+def kernel_times(evs):
+    """Mean milliseconds of (tile scan, verification, sort) over the steps."""
+    tile = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ver = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    srt = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    return tile, ver, srt
+
+
+def per_kernel_roofline(n, m, cands, scan_kernels, sort_kernels, tile_kernel, tile_ms, verify_ms,
+                        sort_ms, peak):
+    """Each kernel of the step against the HBM peak with its own algorithmic
+    bytes: the tile scan reads the text once and writes 16 bytes per listed
+    candidate (8 per match when it verifies itself); the verification kernel
+    reads the list and writes 8 bytes per match; the sort reads and writes
+    each 8-byte key once."""
+    def row(kind, ms, nbytes, rule):
+        gbps = nbytes / ms / 1e6 if ms > 0 else None
+        return {"kernel": kind, "ms": ms, "algorithmic_bytes": nbytes, "achieved_gbps": gbps,
+                "frac": gbps / peak if gbps else None, "bytes_rule": rule}
+    out = {}
+    if scan_kernels == 2:
+        out["tile_scan"] = row(tile_kernel, tile_ms, n + 16 * cands,
+                               "text once + 16 B per listed candidate")
+        out["verify"] = row("rk_verify_kernel", verify_ms, 16 * cands + 8 * m,
+                            "16 B per candidate read + 8 B per match written")
+    else:
+        out["tile_scan"] = row(tile_kernel, tile_ms + verify_ms, n + 8 * m,
+                               "text once + 8 B per match")
+    sort_name = "rk_sort_fused_kernel" if sort_kernels == 1 else "rk_sort_hist/pass kernels"
+    out["sort"] = row(sort_name, sort_ms, 16 * m, "8 B per key read + 8 B written")
+    out["sort"]["launches"] = sort_kernels
+    return out
+
+
+def tile_kernel_name(info_t):
+    return "rk_scan_rf_kernel" if info_t.get("role_step", 0) in (2, 4) else "rk_scan_tiles_kernel"
 
 
 # ---------------------------------------------------------------- replicas
@@ -220,7 +322,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": config_dict(w.n, len(w.patterns)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "build": "gcc " + " ".join(oracle_build.CFLAGS), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -279,12 +381,19 @@ def measure_batched(torch, rk, dev, max_len, reps=5, tune_candidates=12):
         for i in range(min(8, n_items)):  # warm-up
             rk.rk_search_device(tabs[i], ptrs[i], lens[i], keys, pcap, infos[i], ws, wsb, st)
         st.synchronize()
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_items + 1)]
         e0.record(st)
+        marks[0].record(st)
         for i in range(n_items):
             rk.rk_search_device(tabs[i], ptrs[i], lens[i], keys, pcap, infos[i], ws, wsb, st)
+            marks[i + 1].record(st)
         e1.record(st)
         st.synchronize()
         plain_ms = e0.elapsed_time(e1)
+        item_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(n_items)]
+        # completion time of each item when all arrive at once and the plain
+        # launches run one after another in submission order
+        done_ms = [marks[0].elapsed_time(marks[i + 1]) for i in range(n_items)]
         plain_count = int(infos[:, 0].sum().item())
     finally:
         for t in tabs:
@@ -298,6 +407,14 @@ def measure_batched(torch, rk, dev, max_len, reps=5, tune_candidates=12):
         "batched_gbps": total / (batch_ms / 1e3) / 1e9, "batched_ms": batch_ms,
         "per_request_gbps": total / (plain_ms / 1e3) / 1e9, "per_request_ms": plain_ms,
         "speedup": plain_ms / batch_ms, "autotuned_scan_ms": tuned_ms,
+        "latency_ms": {
+            "batched_every_item": batch_ms,
+            "per_request_launch_p50": float(np.percentile(item_ms, 50)),
+            "per_request_launch_p99": float(np.percentile(item_ms, 99)),
+            "per_request_completion_p50": float(np.percentile(done_ms, 50)),
+            "per_request_completion_p99": float(np.percentile(done_ms, 99)),
+            "note": "all texts submitted at once: a batched item completes with the batch; "
+                    "a plain launch's completion includes the launches queued before it"},
         "tuned": {k: info[k] for k in ("warps", "tile_bytes", "stages", "ctas_per_sm",
                                        "s2_in_smem")},
     }
@@ -455,52 +572,125 @@ def measure_paper_kernel(torch, rk, dev, reps=5):
     return out
 
 
+def read_profile_at(path):
+    """read_profile for another committed summary."""
+    global PROFILE
+    keep = PROFILE
+    try:
+        PROFILE = path
+        return read_profile()
+    finally:
+        PROFILE = keep
+
+
+def measure_signature_set(torch, rk, dev, peak, peak_src, steps=10, warmup=3, pool=None,
+                          cores=1, n=None):
+    """The 4 GiB signature set (uniform bytes, 10,000 patterns of 8..64
+    bytes, 1,000 plants each): the same step as the headline line (tile
+    scan, verification, sort over the resident text), each kernel timed with
+    CUDA events, with its own roofline and, given a process pool, the oracle
+    timed on slices of the same text."""
+    from workloads import make_config
+    w = make_config(2, n=n) if n else make_config(2)
+    n = w.n
+    st = torch.cuda.Stream(dev)
+    d = torch.from_numpy(w.text).to(dev)
+    table = rk.rk_build(w.patterns)
+    try:
+        info_t = rk.rk_table_info(table)
+        b = StepBuffers(torch, rk, table, d, n, dev, st, cap=1 << 24)
+        for _ in range(warmup):
+            scan_sort(rk, table, d, n, b, st)
+        evs = new_events(torch, steps)
+        create_events(evs, st)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(steps):
+            scan_sort(rk, table, d, n, b, st, evs[i])
+        e1.record(st)
+        st.synchronize()
+        step_ms = e0.elapsed_time(e1) / steps
+        tile_ms, verify_ms, sort_ms = kernel_times(evs)
+        m = int(b.info[0].item())
+        cands = b.candidates(torch)
+        rows = per_kernel_roofline(n, m, cands, b.scan_kernels, b.sort_kernels,
+                                   tile_kernel_name(info_t), tile_ms, verify_ms, sort_ms, peak)
+        scan_ms = statistics.mean(e[0].elapsed_time(e[2]) for e in evs)
+        launches = b.scan_kernels + b.sort_kernels
+        del b
+    finally:
+        rk.rk_destroy(table)
+        del d
+    tile = rows["tile_scan"]
+    prof = read_profile_at(PROFILE_SIG) or {}
+    out = {
+        "workload": "signature_set_4GiB_10000_patterns_len8-64_uniform_bytes",
+        "text_bytes": n, "patterns": len(w.patterns), "matches": m, "candidates": cands,
+        "value": n / step_ms / 1e6, "unit": UNIT, "ms_per_step": step_ms, "steps": steps,
+        "warmup": warmup, "scan_ms": scan_ms, "gpu_launches_per_step": launches,
+        "table": {kk: info_t[kk] for kk in ("filter", "filter_log2_bits", "role_step",
+                                             "role_filter_log2_bits", "warps", "tile_bytes",
+                                             "stages", "sample_step", "sample_filter_log2_bits")},
+        "roofline": {"bound": "hbm", "achieved": tile["achieved_gbps"], "peak": peak,
+                     "unit": "GB/s", "frac": tile["frac"],
+                     "traffic": prof.get("dram_bytes_per_full_launch"),
+                     "kernel": tile["kernel"], "peak_source": f"{peak_src} hbm_gbs",
+                     "algorithmic_bytes_per_launch": tile["algorithmic_bytes"],
+                     "bytes_rule": tile["bytes_rule"],
+                     "scan_step_frac": (n + 8 * m) / scan_ms / 1e6 / peak,
+                     "per_kernel": rows,
+                     "integer_pipes": None if prof.get("tile_scan_alu_pipe_frac") is None else {
+                         "alu_pipe_frac": prof["tile_scan_alu_pipe_frac"],
+                         "fmaheavy_pipe_frac": prof["tile_scan_fmaheavy_pipe_frac"],
+                         "issue_active_frac": prof["tile_scan_issue_active_frac"],
+                         "warp_instructions_per_byte": prof.get("tile_scan_warp_inst_per_byte"),
+                         "source": os.path.relpath(PROFILE_SIG, ROOT)}},
+        "l2": "text (4 GiB) larger than the 129 MB L2; no flush needed",
+    }
+    if pool is not None:
+        per_core = SIG_CPU_SAMPLE_PER_CORE
+        lmax = max(len(p) for p in w.patterns)
+        slices = cpu_slices(w.text, lmax, per_core, cores, seed=21)
+        wall = time_oracle(pool, slices, w.patterns)
+        out["cpu_baseline"] = {"value": cores * per_core / wall / 1e9, "unit": UNIT,
+                               "cores": cores, "kind": "oracle",
+                               "sample": f"{cores} slices of {per_core} bytes (one per core) at "
+                                         f"random offsets of the 4 GiB text, all 10,000 "
+                                         f"patterns; {SLICE_HALO_NOTE}"}
+    del w
+    return out
+
+
 def measure_plain_configs(torch, rk, dev, hbm_gbs, reps=5):
-    """The other two plain configurations (the bench line itself is the Zipf
-    scan): searches (scan + sort) over the resident text, timed with CUDA
-    events; GB/s = text bytes / search time, and the scan alone against the
-    HBM peak (text read once + 8 bytes per match)."""
+    """The small plain configuration (1 MiB DNA text, 8 patterns of 16
+    bytes): the same step, timed with CUDA events; GB/s = text bytes / step
+    time (the text fits in L2, so its HBM fraction means little)."""
     from workloads import make_config
     st = torch.cuda.Stream(dev)
     out = {}
-    for i, name in ((0, "dna_1MiB_8x16"), (2, "signature_set_4GiB_10000x8-64")):
-        w = make_config(i)
-        d = torch.from_numpy(w.text).to(dev)
-        table = rk.rk_build(w.patterns)
-        cap = 1 << 16
-        scan_b = rk.rk_scan_workspace_bytes(table, w.n)
-        while True:
-            keys = torch.empty(cap, dtype=torch.int64, device=dev)
-            info = torch.zeros(2, dtype=torch.int64, device=dev)
-            wsb = rk.rk_workspace_bytes(table, cap)
-            ws = torch.empty(wsb + scan_b, dtype=torch.uint8, device=dev)
-            rk.rk_search_device(table, d, w.n, keys, cap, info, ws, wsb + scan_b, st)
-            st.synchronize()
-            m = int(info[0])
-            if m <= cap:
-                break
-            cap = m + 1024
-        sws = ws[wsb:]  # the scan's candidate list after the sort workspace
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        scan_ms, search_ms = [], []
-        for _ in range(reps + 1):
-            ev[0].record(st)
-            rk.rk_scan_device_ws(table, d, w.n, keys, cap, info, sws, scan_b, st)
-            ev[1].record(st)
-            rk.rk_sort_device(table, w.n, keys, cap, info, ws, wsb, st)
-            ev[2].record(st)
-            st.synchronize()
-            scan_ms.append(ev[0].elapsed_time(ev[1]))
-            search_ms.append(ev[0].elapsed_time(ev[2]))
-        scan = statistics.median(scan_ms[1:])
-        search = statistics.median(search_ms[1:])
-        out[name] = {"text_bytes": w.n, "patterns": len(w.patterns), "matches": m,
-                     "scan_kernels": rk.rk_scan_launches(table, w.n, scan_b),
-                     "search_ms": search, "gbps": w.n / search / 1e6,
-                     "scan_ms": scan, "scan_gbps_algorithmic": (w.n + 8 * m) / scan / 1e6,
-                     "scan_frac_of_hbm": (w.n + 8 * m) / scan / 1e6 / hbm_gbs}
+    w = make_config(0)
+    d = torch.from_numpy(w.text).to(dev)
+    table = rk.rk_build(w.patterns)
+    try:
+        b = StepBuffers(torch, rk, table, d, w.n, dev, st, cap=1 << 16)
+        for _ in range(3):
+            scan_sort(rk, table, d, w.n, b, st)
+        evs = new_events(torch, reps)
+        create_events(evs, st)
+        for i in range(reps):
+            scan_sort(rk, table, d, w.n, b, st, evs[i])
+        st.synchronize()
+        tile_ms, verify_ms, sort_ms = kernel_times(evs)
+        step = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+        out["dna_1MiB_8x16"] = {"text_bytes": w.n, "patterns": len(w.patterns),
+                                "matches": int(b.info[0].item()), "search_ms": step,
+                                "gbps": w.n / step / 1e6, "tile_scan_ms": tile_ms,
+                                "verify_ms": verify_ms, "sort_ms": sort_ms,
+                                "launches": b.scan_kernels + b.sort_kernels}
+        del b
+    finally:
         rk.rk_destroy(table)
-        del d, keys, ws
     return out
 
 
@@ -528,7 +718,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    w = make_config(1)
+    w = make_config(1, n=args.text_mib << 20) if args.text_mib else make_config(1)
     n, k = w.n, len(w.patterns)
     t0 = time.perf_counter()
     table = rk.rk_build(w.patterns)
@@ -537,40 +727,11 @@ def run_ours(args, rank, world, local_rank):
 
     d_text = torch.from_numpy(w.text).to(dev)
     st = torch.cuda.Stream(dev)
-    d_info = torch.zeros(2, dtype=torch.int64, device=dev)
-
-    # size the output from one probe run; the workspace holds the sort's
-    # scratch and, after it, the deferred scan's candidate list
-    cap = 1 << 22
-    scan_b = rk.rk_scan_workspace_bytes(table, n)
-    while True:
-        keys = torch.empty(cap, dtype=torch.int64, device=dev)
-        wsb = rk.rk_workspace_bytes(table, cap)
-        ws = torch.empty(wsb + scan_b, dtype=torch.uint8, device=dev)
-        rk.rk_search_device(table, d_text, n, keys, cap, d_info, ws, wsb + scan_b, st)
-        st.synchronize()
-        m, status = (int(v) for v in d_info.cpu().tolist())
-        assert status == rk.RK_OK, rk.strerror(status)
-        if m <= cap:
-            break
-        cap = m + 1024
-
-    sws = ws[wsb:]
-    scan_kernels = rk.rk_scan_launches(table, n, scan_b)
-    sort_kernels = rk.rk_sort_launches(table, n, cap)
-
-    def step(evs=None):
-        if evs:
-            evs[0].record(st)
-        rk.rk_scan_device_ws(table, d_text, n, keys, cap, d_info, sws, scan_b, st)
-        if evs:
-            evs[1].record(st)
-        rk.rk_sort_device(table, n, keys, cap, d_info, ws, wsb, st)
-        if evs:
-            evs[2].record(st)
+    bufs = StepBuffers(torch, rk, table, d_text, n, dev, st)
+    cap = bufs.cap
 
     for _ in range(args.warmup):
-        step()
+        scan_sort(rk, table, d_text, n, bufs, st)
     torch.cuda.synchronize()
 
     gpu_id = None
@@ -581,7 +742,8 @@ def run_ours(args, rank, world, local_rank):
     sampler = ClockSampler(gpu_id)
     time.sleep(0.3)
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = new_events(torch, args.steps)
+    create_events(evs, st)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -589,15 +751,17 @@ def run_ours(args, rank, world, local_rank):
     ev_end = torch.cuda.Event(enable_timing=True)
     ev_start.record(st)
     for i in range(args.steps):
-        step(evs[i])
+        scan_sort(rk, table, d_text, n, bufs, st, evs[i])
     ev_end.record(st)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     total_ms = ev_start.elapsed_time(ev_end)
-    scan_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    sort_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    m = int(d_info[0].item())
+    tile_ms, verify_ms, sort_ms = kernel_times(evs)
+    scan_steps = [e[0].elapsed_time(e[2]) for e in evs]
+    m = int(bufs.info[0].item())
+    cands = bufs.candidates(torch)
+    scan_kernels, sort_kernels = bufs.scan_kernels, bufs.sort_kernels
 
     # end to end through the host-buffer call: pinned text in, sorted list out
     e2e_s = float("nan")
@@ -614,20 +778,25 @@ def run_ours(args, rank, world, local_rank):
             assert rc == rk.RK_OK and cnt == m
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     clocks = sampler.stop()
+    del d_text, bufs
 
+    peak, peak_src = hbm_peak()
     extra = {}
     # the extra workloads are single-GPU measurements: at N > 1 the other ranks
     # would wait for them inside the max-over-ranks collective
     if rank == 0 and world == 1 and not args.no_extras:
-        for name, fn in (("batched", lambda: measure_batched(torch, rk, dev, 2 << 20)),
+        for name, fn in (("signature_set", lambda: measure_signature_set(
+                              torch, rk, dev, peak, peak_src, pool=pool, cores=cores)),
+                         ("batched", lambda: measure_batched(torch, rk, dev, 16 << 20)),
                          ("served", lambda: measure_serving(torch, rk, dev)),
                          ("paper_kernel", lambda: measure_paper_kernel(torch, rk, dev)),
                          ("plain_configs",
-                          lambda: measure_plain_configs(torch, rk, dev, hbm_peak()[0]))):
+                          lambda: measure_plain_configs(torch, rk, dev, peak))):
             try:
                 extra[name] = fn()
             except Exception as exc:  # a failed extra must not lose the main line
                 extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
 
     total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
 
@@ -639,19 +808,20 @@ def run_ours(args, rank, world, local_rank):
 
     step_ms = total_ms / args.steps
     value = job_gbps(world, n, args.steps, total_ms)
-    scan_mean_s = statistics.mean(scan_ms) / 1e3
-    alg_bytes = n + 8 * m
-    peak, peak_src = hbm_peak()
-    achieved = alg_bytes / scan_mean_s / 1e9
+    rows = per_kernel_roofline(n, m, cands, scan_kernels, sort_kernels, tile_kernel_name(info_t),
+                               tile_ms, verify_ms, sort_ms, peak)
+    tile = rows["tile_scan"]
     prof = read_profile() or {}
     traffic = prof.get("dram_bytes_per_full_launch")
     pipes = None
     if prof.get("tile_scan_alu_pipe_frac") is not None:
-        pipes = {"kernel": "rk_scan_tiles_kernel",
+        pipes = {"kernel": tile["kernel"],
                  "alu_pipe_frac": prof["tile_scan_alu_pipe_frac"],
                  "fmaheavy_pipe_frac": prof["tile_scan_fmaheavy_pipe_frac"],
                  "issue_active_frac": prof["tile_scan_issue_active_frac"],
-                 "source": "ncu --set full of the same scan step (profiles/rk_scan_zipf_1GiB.md)"}
+                 "warp_instructions_per_byte": prof.get("tile_scan_warp_inst_per_byte"),
+                 "source": f"ncu --set full of the tile scan kernel ({os.path.relpath(PROFILE, ROOT)})"}
+    scan_step_ms = statistics.mean(scan_steps)
 
     cpu = None
     if pool is not None:
@@ -662,7 +832,7 @@ def run_ours(args, rank, world, local_rank):
         one_s, _ = _oracle_slice((slices[0], w.patterns))  # one core, in this process
         cpu = {"value": cores * CPU_SAMPLE_PER_CORE / wall / 1e9, "unit": UNIT, "cores": cores,
                "value_one_core": CPU_SAMPLE_PER_CORE / one_s / 1e9,
-               "kind": "oracle",
+               "kind": "oracle", "build": "gcc " + " ".join(oracle_build.CFLAGS),
                "sample": f"{cores} slices of {CPU_SAMPLE_PER_CORE} bytes (one per core) at random "
                          f"offsets of the 1 GiB text, all 100 patterns; {SLICE_HALO_NOTE}"}
 
@@ -670,21 +840,26 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": dict(config_dict(n, k), parallelism=f"replicas{world}"),
-        "matches": m,
-        "scan_ms": statistics.mean(scan_ms), "sort_ms": statistics.mean(sort_ms),
-        "scan_ms_p10_p90": [float(np.percentile(scan_ms, 10)), float(np.percentile(scan_ms, 90))],
+        "config": config_dict(n, k), "replicas": world,
+        "matches": m, "candidates": cands,
+        "scan_ms": scan_step_ms, "tile_scan_ms": tile_ms, "verify_ms": verify_ms,
+        "sort_ms": sort_ms,
+        "scan_ms_p10_p90": [float(np.percentile(scan_steps, 10)),
+                            float(np.percentile(scan_steps, 90))],
         "hbm_frac_whole_step": (n + 8 * m) / (step_ms / 1e3) / 1e9 / peak,
         "build_ms": build_ms,
-        "table": {kk: info_t[kk] for kk in ("filter", "filter_log2_bits", "warps", "tile_bytes",
-                                             "stages", "ctas_per_sm", "smem_bytes", "s2_smem_bytes",
-                                             "sm_count")},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": ("rk_scan_tiles_kernel + rk_verify_kernel (timed together)"
-                                if scan_kernels == 2 else "rk_scan_tiles_kernel"),
+        "table": {kk: info_t[kk] for kk in ("filter", "filter_log2_bits", "role_step",
+                                             "role_filter_log2_bits", "survivor_warps", "warps",
+                                             "tile_bytes", "stages", "ctas_per_sm", "smem_bytes",
+                                             "s2_smem_bytes", "sm_count")},
+        "roofline": {"bound": "hbm", "achieved": tile["achieved_gbps"], "peak": peak,
+                     "unit": "GB/s", "frac": tile["frac"], "traffic": traffic,
+                     "kernel": tile["kernel"],
                      "peak_source": f"{peak_src} hbm_gbs",
-                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "algorithmic_bytes_per_launch": tile["algorithmic_bytes"],
+                     "bytes_rule": tile["bytes_rule"],
+                     "scan_step_frac": (n + 8 * m) / scan_step_ms / 1e6 / peak,
+                     "per_kernel": rows,
                      "integer_pipes": pipes},
         "e2e": None if args.no_e2e else {
             "value": job_gbps(world, n, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
@@ -711,8 +886,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and served comparisons")
-    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
-                    help="batched: the full 4096-text batch (up to 16 MiB per text) alone")
+    ap.add_argument("--text-mib", type=int, default=0,
+                    help="profiling: the plain or signature workload on a text of this many "
+                         "MiB (same generator and density) instead of the full one; the "
+                         "batched workload with texts of at most this many MiB")
+    ap.add_argument("--workload", choices=["plain", "batched", "signature"], default="plain",
+                    help="batched: the 4096-text batch (up to 16 MiB per text) alone; "
+                         "signature: the 4 GiB signature set alone")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -723,6 +903,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched_full(args)
+    if args.workload == "signature":
+        return run_signature_full(args)
     return run_ours(args, rank, world, local_rank)
 
 
@@ -732,13 +914,37 @@ def run_batched_full(args):
     build_lib.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    r = measure_batched(torch, rk, dev, 16 << 20, reps=max(3, min(args.steps, 20)))
+    r = measure_batched(torch, rk, dev, (args.text_mib or 16) << 20,
+                        reps=max(3, min(args.steps, 20)))
     line = {"metric": METRIC + " [batched workload]", "value": r["batched_gbps"], "unit": UNIT,
             "n_gpus": 1, "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
             "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": r["workload"], "text_bytes": r["text_bytes"]},
             "batched": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_signature_full(args):
+    """The 4 GiB signature set as its own line (one GPU)."""
+    import torch
+    from paper_1810_01051_gb300 import build_lib, rk
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peak, src = hbm_peak()
+    steps = max(1, min(args.steps, 50))
+    r = measure_signature_set(torch, rk, dev, peak, src, steps=steps, warmup=args.warmup,
+                              n=(args.text_mib << 20) or None)
+    line = {"metric": METRIC + " [signature set]", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": r["workload"], "text_bytes": r["text_bytes"],
+                       "patterns": r["patterns"], "l2": r["l2"]},
+            "roofline": r["roofline"], "gpu_launches": steps * r["gpu_launches_per_step"],
+            "signature_set": r}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -224,6 +224,20 @@ int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint64_t n, uint
                       uint64_t capacity, uint64_t *d_info, void *d_workspace,
                       uint64_t workspace_bytes, void *stream);
 
+/* rk_scan_device_ws that also records the CUDA event mid_event (a
+ * cudaEvent_t created by the caller on the current device; NULL: none) on
+ * the stream after the tile scan is launched and before the verification
+ * kernel is, so that events recorded around the call time the two kernels
+ * apart.  When the scan runs as one kernel the event is recorded after it.
+ * On return from a deferring call the workspace's first 8 bytes hold, once
+ * the stream reaches them, the number of candidate windows the tile scan
+ * listed (a uint64_t; it may exceed the list's room).
+ * Errors: as rk_scan_device_ws; RK_ECUDA if the event cannot be recorded.   */
+int rk_scan_device_ws_split(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                            uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                            void *d_workspace, uint64_t workspace_bytes, void *stream,
+                            void *mid_event);
+
 /* Kernels rk_scan_device_ws launches for a text of n bytes and a workspace
  * of workspace_bytes: 2 (tile scan + verification) when it defers, 1 when it
  * runs rk_scan_device, 0 for an empty text or table (memory clears are not

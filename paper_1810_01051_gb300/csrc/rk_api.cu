@@ -91,13 +91,16 @@ bool cand_list(const rk_table *t, uint64_t n, void *ws, uint64_t ws_bytes, CandL
 }
 
 // Scan with the survivors' hash/probe/verify in a second kernel.
+// `mid` (optional) is recorded between the two launches.
 int deferred_scan(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_t *d_keys,
-                  uint64_t capacity, uint64_t *d_info, const CandList &cl, cudaStream_t st) {
+                  uint64_t capacity, uint64_t *d_info, const CandList &cl, cudaStream_t st,
+                  cudaEvent_t mid = nullptr) {
     if (cudaMemsetAsync(d_info, 0, 2 * sizeof(uint64_t), st) != cudaSuccess ||
         cudaMemsetAsync(cl.count, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return RK_ECUDA;
     int rc = launch_scan(t, d_text, n, 0, n, d_keys, capacity, d_info, st, &cl);
     if (rc) return rc;
+    if (mid && cudaEventRecord(mid, st) != cudaSuccess) return RK_ECUDA;
     return launch_verify(t, d_text, n, cl, d_keys, capacity, d_info, st);
 }
 
@@ -126,6 +129,22 @@ extern "C" int rk_scan_device_ws(const rk_table *t, const uint8_t *d_text, uint6
         return rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
     return deferred_scan(t, d_text, n, d_keys, capacity, d_info, cl,
                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rk_scan_device_ws_split(const rk_table *t, const uint8_t *d_text, uint64_t n,
+                                       uint64_t *d_keys, uint64_t capacity, uint64_t *d_info,
+                                       void *d_workspace, uint64_t workspace_bytes, void *stream,
+                                       void *mid_event) {
+    int rc = scan_args_ok(t, d_text, n, d_keys, capacity, d_info);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t mid = reinterpret_cast<cudaEvent_t>(mid_event);
+    CandList cl;
+    if (cand_list(t, n, d_workspace, workspace_bytes, &cl))
+        return deferred_scan(t, d_text, n, d_keys, capacity, d_info, cl, st, mid);
+    rc = rk_scan_device(t, d_text, n, d_keys, capacity, d_info, stream);
+    if (rc == RK_OK && mid && cudaEventRecord(mid, st) != cudaSuccess) return RK_ECUDA;
+    return rc;
 }
 
 extern "C" int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n,

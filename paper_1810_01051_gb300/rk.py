@@ -37,7 +37,7 @@ EXPORTS = [
     "rk_batch_autotune", "rk_server_create", "rk_server_destroy", "rk_server_submit",
     "rk_server_take", "rk_server_stats_get", "rk_paper_search_device",
     "rk_debug_scan_withheld", "rk_build_ptrs", "rk_search_matches", "rk_search_device_matches",
-    "rk_free_matches", "rk_debug_binary_version",
+    "rk_free_matches", "rk_debug_binary_version", "rk_scan_device_ws_split",
 ]
 
 
@@ -143,6 +143,8 @@ def load() -> ctypes.CDLL:
     L.rk_scan_launches.argtypes = [vp, u64, u64, ctypes.POINTER(u32)]
     L.rk_scan_device_ws.restype = ctypes.c_int
     L.rk_scan_device_ws.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp]
+    L.rk_scan_device_ws_split.restype = ctypes.c_int
+    L.rk_scan_device_ws_split.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp, vp]
     L.rk_sort_device.restype = ctypes.c_int
     L.rk_sort_device.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp]
     L.rk_search_device.restype = ctypes.c_int
@@ -354,6 +356,24 @@ def rk_scan_device_ws(table: int, d_text, n: int, d_keys, capacity: int, d_info,
                                     _buf(d_workspace, workspace_bytes, "d_workspace", True),
                                     workspace_bytes, _stream(stream)),
            "rk_scan_device_ws")
+
+
+def rk_scan_device_ws_split(table: int, d_text, n: int, d_keys, capacity: int, d_info,
+                            d_workspace, workspace_bytes: int, stream=None, mid_event=None) -> None:
+    """rk_scan_device_ws recording `mid_event` (a torch.cuda.Event that has
+    been recorded once, so that it exists, or a raw cudaEvent_t) between the
+    tile scan and the verification kernel."""
+    ev = None
+    if mid_event is not None:
+        ev = int(getattr(mid_event, "cuda_event", mid_event))
+        if not ev:
+            raise ValueError("mid_event: the event has not been created (record it once first)")
+    _check(load().rk_scan_device_ws_split(table, _buf(d_text, n, "d_text", True), n,
+                                          _buf(d_keys, 8 * capacity, "d_keys", True), capacity,
+                                          _buf(d_info, 16, "d_info", True),
+                                          _buf(d_workspace, workspace_bytes, "d_workspace", True),
+                                          workspace_bytes, _stream(stream), ev),
+           "rk_scan_device_ws_split")
 
 
 def rk_sort_device(table: int, n: int, d_keys, capacity: int, d_info, d_workspace,

@@ -83,6 +83,7 @@ def test_entry_points_reject_null_table(lib):
     assert lib.rk_scan_workspace_bytes(None, 10) == 0
     assert lib.rk_scan_launches(None, 10, 10, None) == rk.RK_EINVAL
     assert lib.rk_scan_device_ws(None, None, 0, None, 0, None, None, 0, None) == rk.RK_EINVAL
+    assert lib.rk_scan_device_ws_split(None, None, 0, None, 0, None, None, 0, None, None) == rk.RK_EINVAL
     lib.rk_destroy(None)
 
 

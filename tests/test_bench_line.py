@@ -18,6 +18,9 @@ import oracle  # noqa: E402
 import workloads  # noqa: E402
 
 
+CANDS = 1234  # candidate windows the fake tile scan reports
+
+
 class FakeEvent:
     clock = 0.0
 
@@ -50,15 +53,23 @@ def fake_rk(expect_m):
 
     rk.rk_build = lambda patterns: 1
     rk.rk_destroy = lambda t: None
-    rk.rk_table_info = lambda t: {"filter": 1, "filter_log2_bits": 14, "warps": 24,
+    rk.rk_table_info = lambda t: {"filter": 1, "filter_log2_bits": 14, "warps": 16,
                                   "tile_bytes": 49152, "stages": 2, "ctas_per_sm": 1,
-                                  "smem_bytes": 216704, "s2_smem_bytes": 14080, "sm_count": 152}
+                                  "smem_bytes": 216704, "s2_smem_bytes": 14080, "sm_count": 152,
+                                  "role_step": 2, "role_filter_log2_bits": 19,
+                                  "survivor_warps": 6}
+
+    def split(t, d, n, keys, cap, info, sws, scan_b, st, mid):
+        state.setdefault("scans", []).append(1)
+        sws[:8].view(torch.int64)[0] = CANDS
+        mid.record(st)
     rk.rk_scan_workspace_bytes = lambda t, n: 256 + (n // 64 + 4096) * 16
     rk.rk_workspace_bytes = lambda t, cap: 16 * cap + 4096
     rk.rk_search_device = rk_search_device
     rk.rk_scan_launches = lambda t, n, b: 2
     rk.rk_sort_launches = lambda t, n, cap: 1
     rk.rk_scan_device_ws = lambda *a: state.setdefault("scans", []).append(1)
+    rk.rk_scan_device_ws_split = split
     rk.rk_sort_device = lambda *a: None
     rk.rk_search = lambda t, h_text, n, h_keys, cap: (0, expect_m)
     rk.strerror = lambda rc: "ok"
@@ -105,13 +116,26 @@ def test_bench_line(monkeypatch, capsys, cpu_baseline):
     assert line["matches"] == expect_m and line["dtype"] == "u8"
     assert len(state["scans"]) == 4 + 3  # warm-up and timed steps
     assert line["gpu_launches"] == 4 * (2 + 1)
-    # each step spans two 0.5 ms event intervals (scan, sort) on the fake clock
-    assert line["scan_ms"] == pytest.approx(0.5) and line["sort_ms"] == pytest.approx(0.5)
+    # each step spans three 0.5 ms event intervals (tile scan, verification,
+    # sort) on the fake clock
+    assert line["scan_ms"] == pytest.approx(1.0) and line["sort_ms"] == pytest.approx(0.5)
+    assert line["tile_scan_ms"] == pytest.approx(0.5) and line["verify_ms"] == pytest.approx(0.5)
+    assert line["candidates"] == CANDS
     roof = line["roofline"]
     assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
-    assert roof["algorithmic_bytes_per_launch"] == small.n + 8 * expect_m
-    assert roof["achieved"] == pytest.approx((small.n + 8 * expect_m) / 0.5e-3 / 1e9)
+    assert roof["kernel"] == "rk_scan_rf_kernel"
+    assert roof["algorithmic_bytes_per_launch"] == small.n + 16 * CANDS
+    assert roof["achieved"] == pytest.approx((small.n + 16 * CANDS) / 0.5e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["scan_step_frac"] == pytest.approx(
+        (small.n + 8 * expect_m) / 1.0e-3 / 1e9 / roof["peak"])
+    pk = roof["per_kernel"]
+    assert set(pk) == {"tile_scan", "verify", "sort"}
+    assert pk["verify"]["algorithmic_bytes"] == 16 * CANDS + 8 * expect_m
+    assert pk["sort"]["algorithmic_bytes"] == 16 * expect_m
+    for row in pk.values():
+        assert row["ms"] == pytest.approx(0.5)
+        assert row["frac"] == pytest.approx(row["algorithmic_bytes"] / 0.5e-3 / 1e9 / roof["peak"])
     prof = bench.read_profile()
     if prof is None:  # figures taken on other sources are not reported
         assert roof["traffic"] is None and roof["integer_pipes"] is None
@@ -124,6 +148,7 @@ def test_bench_line(monkeypatch, capsys, cpu_baseline):
         cpu = line["cpu_baseline"]
         assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
         assert cpu["value_one_core"] > 0 and "slices" in cpu["sample"]
+        assert cpu["build"].startswith("gcc -O3")
     else:
         assert line["cpu_baseline"] is None
     assert np.isfinite(line["value"]) and line["value"] > 0
