@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle_pool import oracle_items
 from workloads import batched, random_small
 
 pytestmark = pytest.mark.gpu
@@ -56,12 +57,14 @@ def run_batch(texts, tables, table_of, misalign=0, autotune=False, **opts):
         rk.rk_tableset_destroy(ts)
 
 
-def check_items(texts, tables, table_of, items, ids, xs, offs):
+def check_items(texts, tables, table_of, items, ids, xs, offs, expect=None):
+    """Every item's slice of the batch list equals the oracle's list for that
+    item (`expect`: the oracle's lists, computed here when not given)."""
     assert np.all(np.diff(offs.astype(np.int64)) >= 0)
     for i, text in enumerate(texts):
         lo, hi = int(offs[i]), int(offs[i + 1])
         assert np.all(items[lo:hi] == i)
-        ei, eo = oracle.rabin_karp(text, tables[table_of[i]])
+        ei, eo = expect[i] if expect is not None else oracle.rabin_karp(text, tables[table_of[i]])
         assert np.array_equal(ids[lo:hi], ei) and np.array_equal(xs[lo:hi], eo), f"item {i}"
 
 
@@ -98,3 +101,17 @@ def test_batch_autotune_keeps_results():
     bt = batched(seed=11, n_items=64, max_len=1 << 18)
     out = run_batch(bt.texts, bt.tables, bt.table_of, autotune=True)
     check_items(bt.texts, bt.tables, bt.table_of, *out[:4])
+
+
+def test_batch_config_full_max_len():
+    """A batch drawn from the batched configuration's recipe at its full text
+    sizes (log-uniform 1 KiB..16 MiB; 512 texts, about 0.9 GB, the largest
+    above 8 MiB), with the default launch shape and autotuned: every item
+    against the oracle, run on every host core."""
+    bt = batched(seed=0x5EED0013, n_items=512, max_len=16 << 20)
+    assert max(t.size for t in bt.texts) > 8 << 20
+    expect = oracle_items([(t, bt.tables[bt.table_of[i]]) for i, t in enumerate(bt.texts)])
+    for autotune in (False, True):
+        out = run_batch(bt.texts, bt.tables, bt.table_of, capacity=1 << 23, autotune=autotune)
+        check_items(bt.texts, bt.tables, bt.table_of, *out[:4], expect=expect)
+        assert out[0].size > 0

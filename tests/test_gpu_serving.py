@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle_pool import oracle_items
 from workloads import serving_tables, serving_texts
 
 pytestmark = pytest.mark.gpu
@@ -117,3 +118,23 @@ def test_text_of_mem_cap_bytes_is_admitted(tables, tableset):
         assert rc == rk.RK_OK and keys.size == 0
     finally:
         rk.rk_server_destroy(s)
+
+
+def test_large_requests_match_oracle():
+    """Requests at the serving configuration's upper sizes (16..64 MiB of
+    uniform bytes) against its 64 resident tables (1..1024 patterns of 4..64
+    bytes), admitted under a 192 MiB cap so that some wait for memory: each
+    list equals the oracle's, run on every host core."""
+    tables = serving_tables()
+    reqs = serving_texts(0x5EED0031, 8, tables, min_len=16 << 20, max_len=64 << 20)
+    assert max(t.size for _, t in reqs) > 48 << 20
+    expect = oracle_items([(text, tables[tid]) for tid, text in reqs])
+    ts = rk.rk_tableset_build(tables)
+    try:
+        out, stats = serve(ts, reqs, mem_cap=192 << 20, max_text_len=64 << 20, engines=2)
+    finally:
+        rk.rk_tableset_destroy(ts)
+    assert stats["requests_done"] == len(reqs)
+    for (tid, text), (keys, _), (ei, eo) in zip(reqs, out, expect):
+        want = (ei.astype(np.uint64) << np.uint64(40)) | eo
+        assert np.array_equal(keys, want), (tid, text.size, keys.size, want.size)

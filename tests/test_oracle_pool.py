@@ -5,7 +5,7 @@ every chunk boundary, a start offset, and the text's ragged end."""
 import numpy as np
 
 import oracle
-from oracle_pool import oracle_matches
+from oracle_pool import oracle_items, oracle_matches
 from workloads import make_config, random_small
 
 
@@ -29,3 +29,18 @@ def test_start_offset_and_tiny_alphabet():
         keep = offs >= start
         got = oracle_matches(w.text, w.patterns, start=start, procs=2, chunk=4093)
         assert np.array_equal(got[0], ids[keep]) and np.array_equal(got[1], offs[keep])
+
+
+def test_items_equal_each_item_alone():
+    """oracle_items: every item against its own set, long items in chunks
+    (matches across the chunk boundaries), empty texts and empty sets."""
+    items = []
+    for i, n in enumerate((0, 5, 9000, 70_001, 30_000)):
+        w = random_small(40 + i, n, 6 + i, 1, 12, alphabet=b"abc", plants=20)
+        items.append((w.text, w.patterns))
+    items.append((items[2][0], []))
+    got = oracle_items(items, procs=3, chunk=4096)
+    assert len(got) == len(items)
+    for (text, pats), (gi, go) in zip(items, got):
+        ei, eo = oracle.rabin_karp(text, pats) if pats else (np.zeros(0), np.zeros(0))
+        assert np.array_equal(gi, ei) and np.array_equal(go, eo)
