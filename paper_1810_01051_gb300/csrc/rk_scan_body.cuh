@@ -500,8 +500,8 @@ __device__ __forceinline__ void consume_tile(const WinCtx &C, const WarpCtx &w, 
 // Stage 1 over sampled positions only (tables with sample == 4, deferred
 // scans): bit i of the result is set when the word at position 4i of the
 // 16-byte chunk may be the gram at offset j < 4 of some pattern.  The flat
-// bit set of the grams has two bits per gram in one word (the second from
-// the hash's top 5 bits): both must be set.
+// bit set of the grams has three bits per gram in one word (the second and
+// third from the hash's bits 27..31 and 22..26): all must be set.
 template <int MODE>
 __device__ __forceinline__ uint32_t stage1_s4(const uint4 v, const uint8_t *sfilt, uint32_t fmask,
                                               uint32_t lane4) {
@@ -513,7 +513,8 @@ __device__ __forceinline__ uint32_t stage1_s4(const uint4 v, const uint8_t *sfil
         const uint32_t a = MODE == kFilterReplicated ? ((hh & fmask) | lane4) : ((hh >> 3) & fmask);
         const uint32_t word = *reinterpret_cast<const uint32_t *>(sfilt + a);
         uint32_t rot = __funnelshift_r(word, word, hh);  // bucket bit -> bit 31
-        if (MODE == kFilterFlat) rot &= __funnelshift_r(word, word, hh >> 27);
+        if (MODE == kFilterFlat)
+            rot &= __funnelshift_r(word, word, hh >> 27) & __funnelshift_r(word, word, hh >> 22);
         acc = __funnelshift_l(rot, acc, 1);  // word i ends in bit i
     }
     return acc;

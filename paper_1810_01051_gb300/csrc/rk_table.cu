@@ -89,10 +89,11 @@ namespace {
 // Stage-1 bit set of `keys` (4-byte little-endian values or q-byte prefixes):
 // the layout (replicated into 32 banks or flat), its size and the device
 // image.  Returns false for an invalid forced size.
-// two_bits (flat layout): each key sets a second bit of the same word, taken
-// from the hash's top 5 bits, and a key passes only when both are set.
+// three_bits (flat layout): each key also sets two more bits of the same
+// word, at the hash's bits 27..31 and 22..26, and a key passes only when all
+// three are set.
 bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_t bits_opt,
-                 bool two_bits, uint32_t *mode, uint32_t *fbits, std::vector<uint32_t> *img,
+                 bool three_bits, uint32_t *mode, uint32_t *fbits, std::vector<uint32_t> *img,
                  uint32_t *fmask) {
     const uint64_t D = keys.size();
     *fbits = bits_opt;
@@ -105,10 +106,10 @@ bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_
         if (*fbits < 10 || *fbits > 15) return false;
     } else {
         *mode = kFilterFlat;
-        // about 1 in 32 bits set (two bits per key: at most 2^19 bits, 64 KiB,
-        // so that two 48 KiB tiles still fit beside it)
+        // about 1 in 32 bits set (three bits per key: at most 2^19 bits,
+        // 64 KiB, so that two 48 KiB tiles still fit beside it)
         if (!*fbits)
-            *fbits = std::min<uint32_t>(two_bits ? 19 : 20,
+            *fbits = std::min<uint32_t>(three_bits ? 19 : 20,
                                         std::max<uint32_t>(15, ceil_log2(32ull * D)));
         if (*fbits < 10 || *fbits > 20) return false;
     }
@@ -123,7 +124,8 @@ bool make_filter(const std::vector<uint32_t> &keys, uint32_t filter_opt, uint32_
         const uint32_t r = hi & 31;
         // stored one place below r: a right rotation by r moves it to bit 31
         bm[word] |= 1u << ((r + 31) & 31);
-        if (two_bits && *mode == kFilterFlat) bm[word] |= 1u << (((hi >> 27) + 31) & 31);
+        if (three_bits && *mode == kFilterFlat)
+            bm[word] |= (1u << (((hi >> 27) + 31) & 31)) | (1u << (((hi >> 22) + 31) & 31));
     }
     if (*mode == kFilterReplicated) {
         img->resize((size_t)W * 32);
@@ -363,7 +365,7 @@ int build_blob(const uint8_t *patterns, const uint32_t *lens, uint32_t k, uint32
             smap[idx] = SampSlot{key, offs[key]};
         }
         // the same layout choice as the prefix bit set, for this key set; a
-        // flat one tests two bits per gram (stage 1 tests 4x fewer positions)
+        // flat one tests three bits per gram (stage 1 tests 4x fewer positions)
         if (!make_filter(skeys, filter_opt, filter_bits_opt, true, &smode, &sbits, &simg,
                          &smask_addr))
             return RK_EINVAL;
