@@ -890,9 +890,11 @@ def main():
                     help="profiling: the plain or signature workload on a text of this many "
                          "MiB (same generator and density) instead of the full one; the "
                          "batched workload with texts of at most this many MiB")
-    ap.add_argument("--workload", choices=["plain", "batched", "signature"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "batched", "signature", "served"],
+                    default="plain",
                     help="batched: the 4096-text batch (up to 16 MiB per text) alone; "
-                         "signature: the 4 GiB signature set alone")
+                         "signature: the 4 GiB signature set alone; served: the serving "
+                         "loop's load sweep alone")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -905,6 +907,8 @@ def main():
         return run_batched_full(args)
     if args.workload == "signature":
         return run_signature_full(args)
+    if args.workload == "served":
+        return run_served_full(args)
     return run_ours(args, rank, world, local_rank)
 
 
@@ -922,6 +926,25 @@ def run_batched_full(args):
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": r["workload"], "text_bytes": r["text_bytes"]},
             "batched": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served_full(args):
+    """The serving workload's load sweep as its own line (one GPU): `value`
+    is the served GB/s at the highest offered load."""
+    import torch
+    from paper_1810_01051_gb300 import build_lib, rk
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = measure_serving(torch, rk, dev)
+    top = r["levels"][-1]
+    line = {"metric": METRIC + " [served workload]", "value": top["served_gbps"], "unit": UNIT,
+            "n_gpus": 1, "steps": r["requests_per_level"], "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "served": r}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -1,11 +1,13 @@
 // Serving loop: search requests arrive with host texts and a resident table
 // id; a worker thread admits them while their texts fit in a device-memory
-// arena (the admission cap), copies the texts on a copy stream, packs the
-// requests whose texts have landed into whichever batch engine is free (each
-// engine: an rk_batch with its own stream and captured graph), and hands each
-// request its sorted match list.  New requests are admitted and copied while
-// earlier batches run (continuous batching); a finished batch frees its
-// requests' memory for the next arrivals.
+// arena (the admission cap), starts their copies on a copy stream, packs
+// admitted requests into whichever batch engine is free (each engine: an
+// rk_batch with its own stream and captured graph; the engine's stream waits
+// on the device for the copies of its requests), and hands each request its
+// sorted match list.  New requests are admitted and copied while earlier
+// batches run (continuous batching); a finished batch frees its requests'
+// memory for the next arrivals.  The worker sleeps until a submission or a
+// finished batch wakes it (a host function queued after each batch).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -14,6 +16,8 @@
 #include <mutex>
 #include <new>
 #include <thread>
+
+#include <sys/prctl.h>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -61,8 +65,14 @@ struct rk_server {
     Clock::time_point t0;
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request *> arrived, copying, ready;
+    std::condition_variable cv_done;
+    std::deque<Request *> arrived, ready;
+    // wake-ups of the worker: submissions, finished batches (from a host
+    // function on the engine's stream, which must not take `mu`: the worker
+    // holds it across CUDA calls on that stream), shutdown
+    std::mutex wake_mu;
+    std::condition_variable cv_wake;
+    bool wake = false;
     std::unordered_map<uint64_t, Request *> finished;
     std::unordered_set<uint64_t> open_ids;  // submitted and not yet taken
     uint64_t next_id = 1;
@@ -74,6 +84,14 @@ struct rk_server {
 
     double now_us() const {
         return std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
+    }
+
+    void kick() {
+        {
+            std::lock_guard<std::mutex> wl(wake_mu);
+            wake = true;
+        }
+        cv_wake.notify_one();
     }
 };
 
@@ -149,8 +167,11 @@ void harvest(rk_server *s, Engine &e) {
     e.busy = false;
 }
 
+void CUDART_CB batch_finished(void *p) { static_cast<rk_server *>(p)->kick(); }
+
 void loop(rk_server *s) {
     cudaSetDevice(s->device);
+    prctl(PR_SET_TIMERSLACK, 1UL, 0UL, 0UL, 0UL);  // timed waits end on time
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         bool progress = false;
@@ -177,23 +198,11 @@ void loop(rk_server *s) {
                 finish(s, r, RK_ECUDA);
                 continue;
             }
-            s->copying.push_back(r);
+            // ready at once: the engine that takes it waits for the copy on
+            // the device
+            s->ready.push_back(r);
         }
-        // 2. texts that have landed become ready, in arrival order
-        while (!s->copying.empty()) {
-            const cudaError_t q = cudaEventQuery(s->copying.front()->copied);
-            if (q == cudaErrorNotReady) break;
-            Request *r = s->copying.front();
-            s->copying.pop_front();
-            progress = true;
-            if (q == cudaSuccess) {
-                s->ready.push_back(r);
-            } else {
-                cudaGetLastError();
-                finish(s, r, RK_ECUDA);
-            }
-        }
-        // 3. finished batches hand back results and memory
+        // 2. finished batches hand back results and memory
         for (Engine &e : s->engines) {
             if (!e.busy) continue;
             const cudaError_t q = cudaEventQuery(e.done);
@@ -209,7 +218,7 @@ void loop(rk_server *s) {
             }
         }
         if (progress) s->cv_done.notify_all();
-        // 4. pack ready requests into free engines
+        // 3. pack ready requests into free engines
         for (Engine &e : s->engines) {
             if (e.busy || s->ready.empty()) continue;
             std::vector<uint32_t> tabs;
@@ -229,11 +238,19 @@ void loop(rk_server *s) {
             }
             if (e.reqs.empty()) continue;
             const double t = s->now_us();
-            for (Request *r : e.reqs) r->t_launch = t;
+            // the item descriptors first (rk_batch_set waits for its upload),
+            // then the stream waits for the texts' copies and runs the batch
             int rc = rk_batch_set(e.b, (uint32_t)e.reqs.size(), tabs.data(), texts.data(),
                                   lens.data(), e.st);
+            for (Request *r : e.reqs) {
+                r->t_launch = t;
+                if (rc == RK_OK && cudaStreamWaitEvent(e.st, r->copied, 0) != cudaSuccess)
+                    rc = RK_ECUDA;
+            }
             if (rc == RK_OK) rc = rk_batch_run(e.b, e.st);
             if (rc == RK_OK && cudaEventRecord(e.done, e.st) != cudaSuccess) rc = RK_ECUDA;
+            if (rc == RK_OK && cudaLaunchHostFunc(e.st, batch_finished, s) != cudaSuccess)
+                rc = RK_ECUDA;
             if (rc != RK_OK) {
                 for (Request *r : e.reqs) finish(s, r, rc);
                 e.reqs.clear();
@@ -245,10 +262,17 @@ void loop(rk_server *s) {
         }
         bool idle = true;
         for (Engine &e : s->engines) idle = idle && !e.busy;
-        if (s->stop && s->arrived.empty() && s->copying.empty() && s->ready.empty() && idle) break;
+        if (s->stop && s->arrived.empty() && s->ready.empty() && idle) break;
         if (!progress) {
-            // nothing changed: wait for a submit, or poll the GPU again shortly
-            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            // nothing changed: sleep until a submission, a finished batch or
+            // shutdown wakes the worker (and look again after 1 ms regardless)
+            lk.unlock();
+            {
+                std::unique_lock<std::mutex> wl(s->wake_mu);
+                s->cv_wake.wait_for(wl, std::chrono::milliseconds(1), [s] { return s->wake; });
+                s->wake = false;
+            }
+            lk.lock();
         }
     }
 }
@@ -324,7 +348,7 @@ extern "C" void rk_server_destroy(rk_server *s) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->stop = true;
         }
-        s->cv_work.notify_all();
+        s->kick();
         s->worker.join();
     }
     for (Engine &e : s->engines) {
@@ -370,7 +394,7 @@ extern "C" int rk_server_submit(rk_server *s, uint32_t table, const uint8_t *h_t
         s->open_ids.insert(r->id);
         *request_id = r->id;
     }
-    s->cv_work.notify_one();
+    s->kick();
     return RK_OK;
 }
 
@@ -415,7 +439,7 @@ extern "C" int rk_server_stats_get(rk_server *s, rk_server_stats *st) {
     r.batches = s->batches;
     r.items_batched = s->items_batched;
     r.waiting = s->arrived.size();
-    r.in_flight = s->copying.size() + s->ready.size();
+    r.in_flight = s->ready.size();
     for (const Engine &e : s->engines) r.in_flight += e.reqs.size();
     r.arena_used = s->arena.used();
     r.now_us = s->now_us();
