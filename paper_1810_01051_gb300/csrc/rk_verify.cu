@@ -31,9 +31,11 @@ struct VerifyParams {
 
 // S2S: the survivor tables (P.tab.s2_bytes) are first copied to the block's
 // dynamic shared memory, so each candidate's chain of table loads stays on
-// chip; otherwise they are read through L1/L2.
+// chip; otherwise they are read through L1/L2.  Eight blocks per SM (32
+// registers a thread): the kernel waits on global loads, and more resident
+// warps hide more of that latency.
 template <bool S2S>
-__global__ void __launch_bounds__(kVerifyThreads)
+__global__ void __launch_bounds__(kVerifyThreads, 8)
     rk_verify_kernel(const __grid_constant__ VerifyParams P) {
     extern __shared__ __align__(128) uint8_t ss2[];
     __shared__ uint32_t mcount[kVerifyWarps];
