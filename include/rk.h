@@ -186,7 +186,7 @@ int rk_scan_device(const rk_table *t, const uint8_t *d_text, uint64_t n, uint64_
 /* Sort the keys left by rk_scan_device ascending (= ascending (id, x)), in
  * place, reading the count from d_info on the device.  Does nothing when
  * d_info[0] > capacity.  n must be the text length given to the scan.
- * Outputs of up to 8 tiles of 2048 keys per resident CTA are sorted by one
+ * Outputs of up to 32 tiles of 2048 keys per resident CTA are sorted by one
  * cooperative launch (all digit passes, grid barriers between phases);
  * larger ones by one decoupled look-back kernel per pass.
  *   d_workspace  at least rk_workspace_bytes(t, capacity) bytes, 16-byte aligned.

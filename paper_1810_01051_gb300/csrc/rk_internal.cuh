@@ -230,7 +230,7 @@ int launch_sort(const rk_table *t, uint64_t n, uint64_t *d_keys, uint64_t capaci
                 const uint64_t *d_info, void *d_ws, uint64_t ws_bytes, cudaStream_t stream);
 
 // Sort keys[0 .. d_info[0]) ascending over the 8-bit digits at the given bit
-// shifts (least significant first).  allow_fused: outputs of up to 8 tiles
+// shifts (least significant first).  allow_fused: outputs of up to 32 tiles
 // per resident CTA may be sorted by one cooperative launch (every pass, grid
 // barriers between phases) instead of one look-back kernel per pass.
 int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, uint64_t *d_keys,

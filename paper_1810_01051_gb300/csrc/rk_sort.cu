@@ -539,12 +539,16 @@ uint32_t fused_grid(int sm_count) {
     return per_sm[dev] * (uint32_t)sm_count;
 }
 
+// Most tiles of 2048 keys per resident CTA that the fused sort takes: with
+// more than one per CTA, phases A and C loop over them (C ranks again).
+constexpr uint64_t kFusedTilesPerCta = 32;
+
 // CTAs of the fused sort for an output of `capacity` keys (0: the look-back
 // kernels are used instead).
 uint32_t fused_ctas(int sm_count, uint64_t capacity, bool allow_fused) {
     const uint32_t gmax = allow_fused ? fused_grid(sm_count) : 0;
     const uint64_t tiles = sort_ws_layout(capacity).tiles;
-    if (!gmax || tiles > 8ull * gmax) return 0;
+    if (!gmax || tiles > kFusedTilesPerCta * gmax) return 0;
     return (uint32_t)std::min<uint64_t>(tiles, gmax);
 }
 
@@ -580,7 +584,7 @@ int launch_sort_shifts(int sm_count, const uint32_t *shifts, uint32_t nshift, ui
 
     if (cudaMemsetAsync(ws + L.ctrl_off, 0, L.status_off - L.ctrl_off, stream) != cudaSuccess)
         return RK_ECUDA;
-    // up to 8 tiles per CTA: every pass in one cooperative launch
+    // up to kFusedTilesPerCta tiles per CTA: every pass in one cooperative launch
     if (const uint32_t g = fused_ctas(sm_count, capacity, allow_fused)) {
         // digit-major counts, 256 x tiles (in the look-back words' space)
         uint32_t *cnt = reinterpret_cast<uint32_t *>(status);

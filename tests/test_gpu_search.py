@@ -179,7 +179,7 @@ def test_scan_then_sort_equals_search():
                          ids=["4-passes", "5-passes"])
 def test_sort_paths_agree(n, k, lmin, lmax):
     """The cooperative single-launch sort (small capacity) and the per-pass
-    look-back kernels (capacity beyond 8 tiles per resident CTA) give the
+    look-back kernels (capacity beyond 32 tiles per resident CTA) give the
     oracle's list on the same keys, with odd and even pass counts and with
     several tiles per CTA (more than two tiles per SM of matches)."""
     torch = pytest.importorskip("torch")
@@ -190,7 +190,7 @@ def test_sort_paths_agree(n, k, lmin, lmax):
     table = rk.rk_build(w.patterns)
     try:
         d = to_device(w.text)
-        for cap, fused in ((m + 100, True), (1 << 24, False)):
+        for cap, fused in ((m + 100, True), (1 << 24, True), (1 << 25, False)):
             launches = rk.rk_sort_launches(table, n, cap)
             assert (launches == 1) == fused, (cap, launches)
             keys, count, status = search_table(table, d, n, cap)
