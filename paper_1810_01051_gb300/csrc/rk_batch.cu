@@ -344,9 +344,14 @@ extern "C" int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, con
     ts->n_tables = n_tables;
     ts->npat.assign(patterns_per_table, patterns_per_table + n_tables);
     ts->filter_mode = filt == RK_FILTER_NONE ? kFilterNone : kFilterFlat;
+    ts->base_log2 = base_log2;
+    ts->pat_first.resize(n_tables);
+    ts->byte_first.resize(n_tables);
     for (uint32_t i = 0; i < n_tables; ++i) {
         const uint32_t k = patterns_per_table[i];
         if (k > RK_MAX_PATTERNS) { delete ts; return RK_EINVAL; }
+        ts->pat_first[i] = pat_off;
+        ts->byte_first[i] = byte_off;
         // table sets are scanned unsampled, with the prefix filter
         int rc = build_blob(patterns + byte_off, lens + pat_off, k, base_log2, filt,
                             o.filter_log2_bits, 1, 1, &blobs[i]);
@@ -362,6 +367,8 @@ extern "C" int rk_tableset_build(uint32_t n_tables, const uint8_t *patterns, con
         ts->max_patterns = std::max(ts->max_patterns, k);
         if (m.q != 4) ts->all_q4 = false;
     }
+    if (byte_off) ts->bytes.assign(patterns, patterns + byte_off);
+    if (pat_off) ts->lens.assign(lens, lens + pat_off);
     const size_t tab_off = size;
     size += ws_align(sizeof(DevTable) * n_tables);
     if (cudaGetDevice(&ts->device) != cudaSuccess ||

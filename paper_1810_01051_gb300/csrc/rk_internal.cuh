@@ -170,7 +170,14 @@ struct rk_tableset {
     uint32_t filter_mode = rk::kFilterFlat;
     uint32_t max_filter_bytes = 0, max_s2_bytes = 0, max_lmax = 1, max_patterns = 0;
     bool all_q4 = true;
+    uint32_t base_log2 = 8;
     std::vector<uint32_t> npat;  // patterns per table
+    // host copy of the patterns (the serving loop builds plain tables from
+    // them): table i's lengths start at lens[pat_first[i]], its bytes at
+    // bytes[byte_first[i]]
+    std::vector<uint8_t> bytes;
+    std::vector<uint32_t> lens;
+    std::vector<uint64_t> pat_first, byte_first;
 };
 
 namespace rk {

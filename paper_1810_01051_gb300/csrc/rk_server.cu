@@ -1,13 +1,15 @@
 // Serving loop: search requests arrive with host texts and a resident table
 // id; a worker thread admits them while their texts fit in a device-memory
-// arena (the admission cap), starts their copies on a copy stream, packs
+// arena (the admission cap), copies the texts on a copy stream, packs
 // admitted requests into whichever batch engine is free (each engine: an
 // rk_batch with its own stream and captured graph; the engine's stream waits
 // on the device for the copies of its requests), and hands each request its
 // sorted match list.  New requests are admitted and copied while earlier
 // batches run (continuous batching); a finished batch frees its requests'
-// memory for the next arrivals.  The worker sleeps until a submission or a
-// finished batch wakes it (a host function queued after each batch).
+// memory for the next arrivals.  A lone request on an idle GPU runs as a
+// plain search with its table's plain build.  The worker polls while work is
+// in flight or recent, else sleeps until a submission or a finished run (a
+// host function queued after each run) wakes it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -27,6 +29,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr double kSpinUs = 2000;  // the worker polls for this long after its last activity
 using rk::Arena;
 
 struct Request {
@@ -50,12 +53,20 @@ struct Engine {
     std::vector<Request *> reqs;
     uint64_t *h_keys = nullptr;     // pinned: the batch's sorted keys
     uint64_t *h_offsets = nullptr;  // pinned: item offsets
+    // a lone request run as a plain search (scan + sort) instead of a batch
+    bool plain = false;
+    uint64_t *d_pkeys = nullptr;    // its sorted keys (batch_capacity of them)
+    uint64_t *d_pinfo = nullptr;    // its {count, status}
+    uint64_t *h_pinfo = nullptr;    // pinned copy of d_pinfo
+    void *d_pws = nullptr;          // its workspace (sort + candidate list)
+    uint64_t pws_bytes = 0;
 };
 
 }  // namespace
 
 struct rk_server {
     const rk_tableset *ts = nullptr;
+    std::vector<rk_table *> plain_tables;  // one per resident table
     rk_server_opts opts{};
     int device = 0;
     uint8_t *arena_mem = nullptr;
@@ -79,6 +90,7 @@ struct rk_server {
     uint32_t batch_limit = 0;  // items per batch after an overflow (0: no limit)
     bool stop = false;
     uint64_t bytes_done = 0, requests_done = 0, batches = 0, items_batched = 0;
+    double t_active = 0;  // last time the worker had work in flight or made progress
     std::vector<cudaEvent_t> spare_events;
     std::thread worker;
 
@@ -169,6 +181,55 @@ void harvest(rk_server *s, Engine &e) {
 
 void CUDART_CB batch_finished(void *p) { static_cast<rk_server *>(p)->kick(); }
 
+// A lone request as a plain search on the engine's stream: wait for its
+// copy, scan + sort with its table's plain build, then the header to the
+// host; the keys are read when the run is done (harvest_plain).
+int launch_plain(rk_server *s, Engine &e, Request *r) {
+    r->t_launch = s->now_us();
+    e.reqs.assign(1, r);
+    e.plain = true;
+    int rc = cudaStreamWaitEvent(e.st, r->copied, 0) == cudaSuccess ? RK_OK : RK_ECUDA;
+    if (rc == RK_OK)
+        rc = rk_search_device(s->plain_tables[r->table], s->arena_mem + r->arena_off, r->n,
+                              e.d_pkeys, s->opts.batch_capacity, e.d_pinfo, e.d_pws,
+                              e.pws_bytes, e.st);
+    if (rc == RK_OK && cudaMemcpyAsync(e.h_pinfo, e.d_pinfo, 16, cudaMemcpyDeviceToHost, e.st) !=
+                           cudaSuccess)
+        rc = RK_ECUDA;
+    if (rc == RK_OK && cudaEventRecord(e.done, e.st) != cudaSuccess) rc = RK_ECUDA;
+    if (rc == RK_OK && cudaLaunchHostFunc(e.st, batch_finished, s) != cudaSuccess) rc = RK_ECUDA;
+    if (rc != RK_OK) {
+        e.reqs.clear();
+        e.plain = false;
+    }
+    return rc;
+}
+
+// Collect a finished plain search (mutex held).
+void harvest_plain(rk_server *s, Engine &e) {
+    Request *r = e.reqs[0];
+    const uint64_t count = e.h_pinfo[0], status = e.h_pinfo[1];
+    int rc = (int)status;
+    if (rc == RK_OK && count > s->opts.batch_capacity) rc = RK_ECAPACITY;
+    if (rc == RK_OK) {
+        r->keys.resize(count);
+        if (count &&
+            (cudaMemcpyAsync(r->keys.data(), e.d_pkeys, 8 * count, cudaMemcpyDeviceToHost, e.st) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(e.st) != cudaSuccess)) {
+            cudaGetLastError();
+            r->keys.clear();
+            rc = RK_ECUDA;
+        }
+    }
+    finish(s, r, rc);
+    s->batches += 1;
+    s->items_batched += 1;
+    e.reqs.clear();
+    e.plain = false;
+    e.busy = false;
+}
+
 void loop(rk_server *s) {
     cudaSetDevice(s->device);
     prctl(PR_SET_TIMERSLACK, 1UL, 0UL, 0UL, 0UL);  // timed waits end on time
@@ -209,18 +270,38 @@ void loop(rk_server *s) {
             if (q == cudaErrorNotReady) continue;
             progress = true;
             if (q == cudaSuccess) {
-                harvest(s, e);
+                if (e.plain) harvest_plain(s, e);
+                else harvest(s, e);
             } else {
                 cudaGetLastError();
                 for (Request *r : e.reqs) finish(s, r, RK_ECUDA);
                 e.reqs.clear();
+                e.plain = false;
                 e.busy = false;
             }
         }
         if (progress) s->cv_done.notify_all();
-        // 3. pack ready requests into free engines
+        // 3. pack ready requests into free engines; a lone request on an
+        // idle GPU (nothing else admitted or waiting) runs as a plain search
+        bool all_idle = true;
+        for (const Engine &e : s->engines) all_idle = all_idle && !e.busy;
         for (Engine &e : s->engines) {
             if (e.busy || s->ready.empty()) continue;
+            if (all_idle && s->ready.size() == 1 && s->arrived.empty() &&
+                s->ready.front()->n > 0) {
+                Request *r = s->ready.front();
+                s->ready.pop_front();
+                const int rc = launch_plain(s, e, r);
+                if (rc != RK_OK) {
+                    finish(s, r, rc);
+                    s->cv_done.notify_all();
+                    continue;
+                }
+                e.busy = true;
+                all_idle = false;
+                progress = true;
+                continue;
+            }
             std::vector<uint32_t> tabs;
             std::vector<const uint8_t *> texts;
             std::vector<uint64_t> lens;
@@ -258,14 +339,24 @@ void loop(rk_server *s) {
                 continue;
             }
             e.busy = true;
+            all_idle = false;
             progress = true;
         }
         bool idle = true;
         for (Engine &e : s->engines) idle = idle && !e.busy;
         if (s->stop && s->arrived.empty() && s->ready.empty() && idle) break;
-        if (!progress) {
-            // nothing changed: sleep until a submission, a finished batch or
-            // shutdown wakes the worker (and look again after 1 ms regardless)
+        const double now = s->now_us();
+        if (progress || !idle) s->t_active = now;
+        if (!progress && now - s->t_active < kSpinUs) {
+            // work in flight, or recent: look again at once, letting
+            // submissions and takes have the lock in between (a sleeping
+            // worker would add two thread wake-ups to every request)
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else if (!progress) {
+            // idle: sleep until a submission, a finished batch or shutdown
+            // wakes the worker (and look again after 1 ms regardless)
             lk.unlock();
             {
                 std::unique_lock<std::mutex> wl(s->wake_mu);
@@ -311,9 +402,35 @@ extern "C" int rk_server_create(const rk_tableset *ts, const rk_server_opts *opt
     int rc = RK_OK;
     if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = RK_ECUDA;
+    // plain builds of the resident tables, for lone requests; their
+    // workspace: the sort's for batch_capacity keys and the candidate list
+    // for max_text_len bytes
+    const rk_tableset *T = ts;
+    s->plain_tables.assign(T->n_tables, nullptr);
+    uint64_t pws = 0;
+    for (uint32_t i = 0; i < T->n_tables && !rc; ++i) {
+        rk_build_opts bo{};
+        bo.base_log2 = T->base_log2;
+        const uint32_t k = T->npat[i];
+        rc = rk_build(k ? T->bytes.data() + T->byte_first[i] : nullptr,
+                      k ? T->lens.data() + T->pat_first[i] : nullptr, k, &bo,
+                      &s->plain_tables[i]);
+        if (!rc)
+            pws = std::max(pws, rk_workspace_bytes(s->plain_tables[i], o.batch_capacity) +
+                                    rk_scan_workspace_bytes(s->plain_tables[i], o.max_text_len));
+    }
     s->engines.resize(o.engines);
     for (Engine &e : s->engines) {
         if (rc) break;
+        e.pws_bytes = pws;
+        if (cudaMalloc(&e.d_pkeys, 8 * o.batch_capacity) != cudaSuccess ||
+            cudaMalloc(&e.d_pinfo, 16) != cudaSuccess ||
+            (pws && cudaMalloc(&e.d_pws, pws) != cudaSuccess) ||
+            cudaMallocHost(&e.h_pinfo, 16) != cudaSuccess) {
+            cudaGetLastError();
+            rc = RK_ENOMEM;
+            break;
+        }
         rk_batch_opts bo{};
         bo.max_items = o.max_batch_items;
         bo.max_text_len = o.max_text_len;
@@ -358,7 +475,12 @@ extern "C" void rk_server_destroy(rk_server *s) {
         if (e.done) cudaEventDestroy(e.done);
         if (e.h_keys) cudaFreeHost(e.h_keys);
         if (e.h_offsets) cudaFreeHost(e.h_offsets);
+        if (e.h_pinfo) cudaFreeHost(e.h_pinfo);
+        cudaFree(e.d_pkeys);
+        cudaFree(e.d_pinfo);
+        cudaFree(e.d_pws);
     }
+    for (rk_table *t : s->plain_tables) rk_destroy(t);
     if (s->copy_stream) {
         cudaStreamSynchronize(s->copy_stream);
         cudaStreamDestroy(s->copy_stream);
