@@ -444,8 +444,12 @@ int rk_batch_autotune(rk_batch *b, uint32_t max_candidates, uint32_t reps, doubl
  * table id) are admitted while their texts fit in a device-memory arena of
  * mem_cap bytes, copied to the device, and packed into batched launches on
  * `engines` batch engines; requests arriving while batches run are admitted
- * and copied meanwhile and go into the next free engine.  Each request gets
- * its own sorted match list in the single-text key format RK_KEY(id, x).   */
+ * and copied meanwhile and go into the next free engine.  A lone request on
+ * an idle GPU runs as a plain search (rk_search_device with a plain build of
+ * its table, made at rk_server_create) and counts as a batch of one.  Each
+ * request gets its own sorted match list in the single-text key format
+ * RK_KEY(id, x).  The worker thread polls while work is in flight and for
+ * 2 ms after, so it keeps one host core busy then.                         */
 typedef struct rk_server rk_server;
 
 typedef struct rk_server_opts {
@@ -469,7 +473,9 @@ typedef struct rk_server_stats {
 } rk_server_stats;
 
 /* Start a server (and its worker thread) on the current device.  The table
- * set must outlive it.  Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA.             */
+ * set must outlive it.  Besides the arena it allocates, per engine, a batch
+ * engine and a plain search's keys (batch_capacity) and workspace (for
+ * max_text_len bytes).  Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA.             */
 int rk_server_create(const rk_tableset *ts, const rk_server_opts *opts, rk_server **out);
 
 /* Finish every submitted request, stop the worker and free everything.     */
