@@ -57,7 +57,8 @@ def fake_rk(expect_m):
                                   "tile_bytes": 49152, "stages": 2, "ctas_per_sm": 1,
                                   "smem_bytes": 216704, "s2_smem_bytes": 14080, "sm_count": 152,
                                   "role_step": 2, "role_filter_log2_bits": 19,
-                                  "survivor_warps": 6}
+                                  "survivor_warps": 6, "sample_step": 1,
+                                  "sample_filter_log2_bits": 0}
 
     def split(t, d, n, keys, cap, info, sws, scan_b, st, mid):
         state.setdefault("scans", []).append(1)
@@ -76,11 +77,9 @@ def fake_rk(expect_m):
     return rk, state
 
 
-@pytest.mark.parametrize("cpu_baseline", [False, True])
-def test_bench_line(monkeypatch, capsys, cpu_baseline):
-    small = workloads.make_config(1, n=1 << 20)
-    expect_m = int(oracle.rabin_karp(small.text, small.patterns)[0].size)
-    rk, state = fake_rk(expect_m)
+def fake_gpu(monkeypatch, rk, small):
+    """Replace the library, CUDA streams, events and device placement with
+    CPU stand-ins, and every configuration with the small workload."""
     pkg = types.SimpleNamespace(rk=rk, build_lib=types.SimpleNamespace(build=lambda: None))
     monkeypatch.setitem(sys.modules, "paper_1810_01051_gb300", pkg)
     monkeypatch.setattr(workloads, "make_config", lambda i, n=None, **k: small)
@@ -98,6 +97,14 @@ def test_bench_line(monkeypatch, capsys, cpu_baseline):
     monkeypatch.setattr(torch.cuda, "get_device_properties",
                         lambda d: types.SimpleNamespace(uuid="fake"))
     monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+
+
+@pytest.mark.parametrize("cpu_baseline", [False, True])
+def test_bench_line(monkeypatch, capsys, cpu_baseline):
+    small = workloads.make_config(1, n=1 << 20)
+    expect_m = int(oracle.rabin_karp(small.text, small.patterns)[0].size)
+    rk, state = fake_rk(expect_m)
+    fake_gpu(monkeypatch, rk, small)
     argv = ["bench.py", "--steps", "4", "--warmup", "3", "--no-extras", "--e2e-steps", "2"]
     if not cpu_baseline:
         argv.append("--no-cpu-baseline")
@@ -152,3 +159,29 @@ def test_bench_line(monkeypatch, capsys, cpu_baseline):
     else:
         assert line["cpu_baseline"] is None
     assert np.isfinite(line["value"]) and line["value"] > 0
+
+
+def test_signature_line(monkeypatch, capsys):
+    """`--workload signature`: the signature-set object as a line of its own,
+    with its per-kernel roofline (on the small workload and the fake GPU)."""
+    small = workloads.make_config(1, n=1 << 20)
+    expect_m = int(oracle.rabin_karp(small.text, small.patterns)[0].size)
+    rk, state = fake_rk(expect_m)
+    fake_gpu(monkeypatch, rk, small)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "signature", "--steps", "3",
+                                      "--warmup", "3"])
+    assert bench.main() == 0
+    out = [line for line in capsys.readouterr().out.splitlines() if line.startswith("{")]
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert line["steps"] == 3 and line["n_gpus"] == 1 and line["dtype"] == "u8"
+    assert line["config"]["text_bytes"] == small.n
+    sig = line["signature_set"]
+    assert sig["matches"] == expect_m and sig["candidates"] == CANDS
+    roof = line["roofline"]
+    assert roof is sig["roofline"] or roof == sig["roofline"]
+    assert set(roof["per_kernel"]) == {"tile_scan", "verify", "sort"}
+    assert roof["algorithmic_bytes_per_launch"] == small.n + 16 * CANDS
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert line["gpu_launches"] == 3 * (2 + 1)
+    assert len(state["scans"]) == 3 + 3  # warm-up and timed steps (split or plain)
