@@ -104,12 +104,12 @@ def scan_sources_sha256():
     return h.hexdigest()
 
 
-def read_profile():
-    """Figures of the committed ncu summary of the scan step, if it was taken
-    on the current scan kernel sources (else None): DRAM bytes per step and
-    the tile scan's integer-pipe fractions."""
+def read_profile(path=None):
+    """Figures of a committed ncu summary (default: the Zipf scan's), if it
+    was taken on the current scan kernel sources (else None): DRAM bytes per
+    full launch and the tile scan's integer-pipe fractions."""
     try:
-        txt = open(PROFILE).read()
+        txt = open(path or PROFILE).read()
     except OSError:
         return None
     m_src = re.search(r"scan_sources_sha256:\s*([0-9a-f]{64})", txt)
@@ -572,17 +572,6 @@ def measure_paper_kernel(torch, rk, dev, reps=5):
     return out
 
 
-def read_profile_at(path):
-    """read_profile for another committed summary."""
-    global PROFILE
-    keep = PROFILE
-    try:
-        PROFILE = path
-        return read_profile()
-    finally:
-        PROFILE = keep
-
-
 def measure_signature_set(torch, rk, dev, peak, peak_src, steps=10, warmup=3, pool=None,
                           cores=1, n=None):
     """The 4 GiB signature set (uniform bytes, 10,000 patterns of 8..64
@@ -623,7 +612,7 @@ def measure_signature_set(torch, rk, dev, peak, peak_src, steps=10, warmup=3, po
         rk.rk_destroy(table)
         del d
     tile = rows["tile_scan"]
-    prof = read_profile_at(PROFILE_SIG) or {}
+    prof = read_profile(PROFILE_SIG) or {}
     out = {
         "workload": "signature_set_4GiB_10000_patterns_len8-64_uniform_bytes",
         "text_bytes": n, "patterns": len(w.patterns), "matches": m, "candidates": cands,
